@@ -1,0 +1,460 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+textbook special cases, exact solutions, invariants, values the paper prints
+(tests/golden/paper_values.json) and brute force on small inputs.  A dropped term,
+a wrong sign, a swapped index or a transposed operand anywhere in the scheme fails at
+least one of them (see the per-test docstrings).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from paper_1607_01105_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def grid_of(pb, **kw):
+    return oracle.Grid(pb.n, pb.h, pb.gamma, pb.bc, pb.cfl,
+                       rho_mean=oracle.mean_density(pb.u), **kw)
+
+
+def parabola_eval(qL, dq, q6, xi):
+    """Eq. A1 of the Appendix: q(xi) = qL + xi (dq + q6 (1 - xi))."""
+    return qL + xi * (dq + q6 * (1.0 - xi))
+
+
+def quad(fn, a, b, n=8):
+    x, w = np.polynomial.legendre.leggauss(n)
+    xs = 0.5 * (a + b) + 0.5 * (b - a) * x
+    return 0.5 * (b - a) * np.sum(w * fn(xs))
+
+
+# ------------------------------------------------------------------ parabolas (S1)
+
+def test_golden_inputs_match_table2():
+    """The generators use the shock-tube states printed in Table 2."""
+    for row, vals in GOLDEN["shock_tubes"]["rows"].items():
+        assert tuple(float(v) for v in vals) == inputs.SOD_TABLE2[int(row)]
+
+
+def test_parabola_constant_is_flat():
+    qL, qR, dq, q6 = oracle.line_parabolas(np.full(12, 3.25))
+    c = slice(2, 10)
+    assert np.all(qL[c] == 3.25) and np.all(qR[c] == 3.25)
+    assert np.all(dq[c] == 0.0) and np.all(q6[c] == 0.0)
+
+
+def test_parabola_linear_exact():
+    """Linear data: faces at the exact point values, q6 = 0, averages exact."""
+    i = np.arange(16, dtype=np.float64)
+    q = 2.0 + 0.75 * i
+    qL, qR, dq, q6 = oracle.line_parabolas(q)
+    for c in range(2, 14):
+        assert qL[c] == pytest.approx(2.0 + 0.75 * (c - 0.5), abs=1e-14)
+        assert qR[c] == pytest.approx(2.0 + 0.75 * (c + 0.5), abs=1e-14)
+        assert abs(q6[c]) < 1e-13
+        y = 0.3
+        # mean of the linear function over the right fraction y of cell c
+        exact_r = 2.0 + 0.75 * (c + 0.5 - 0.5 * y)
+        exact_l = 2.0 + 0.75 * (c - 0.5 + 0.5 * y)
+        assert oracle.avg_right_part(qR[c], dq[c], q6[c], y) == pytest.approx(exact_r, abs=1e-13)
+        assert oracle.avg_left_part(qL[c], dq[c], q6[c], y) == pytest.approx(exact_l, abs=1e-13)
+
+
+def test_face_interpolant_exact_for_cubics():
+    """Appendix: the 4th-order face formula from cell averages reproduces a cubic's point
+    values at the faces (unlimited slopes on monotone data).  Catches a wrong 1/2 or 1/6
+    coefficient, a swapped delta index or a sign error in the face formula."""
+    h = 0.05
+    poly = np.polynomial.Polynomial([0.3, 1.0, 0.4, 0.2])  # increasing on [0, 1]
+    P = poly.integ()
+    edges = np.arange(21) * h
+    q = (P(edges[1:]) - P(edges[:-1])) / h
+    qL, qR, dq, q6 = oracle.line_parabolas(q)
+    for c in range(3, 17):
+        assert qR[c] == pytest.approx(poly(edges[c + 1]), abs=1e-12)
+        assert qL[c] == pytest.approx(poly(edges[c]), abs=1e-12)
+
+
+def test_parabola_conserves_cell_average_random():
+    """Appendix (integral property below eq. A1): the mean of every final parabola over
+    its cell equals the cell value.  Checked by quadrature of eq. A1 with the returned
+    coefficients; a wrong q6 or Delta q (e.g. the printed qL - qR sign) fails it."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        q = rng.normal(size=40) * rng.uniform(0.1, 10)
+        qL, qR, dq, q6 = oracle.line_parabolas(q)
+        for c in range(2, 38):
+            m = quad(lambda x: parabola_eval(qL[c], dq[c], q6[c], x), 0.0, 1.0, 4)
+            assert m == pytest.approx(q[c], rel=1e-12, abs=1e-12)
+            assert qR[c] == pytest.approx(parabola_eval(qL[c], dq[c], q6[c], 1.0), abs=1e-12)
+
+
+def test_parabola_monotone_no_new_extrema():
+    """Appendix Step 2: after the monotonicity fixes each parabola is monotone on its cell
+    and stays within the range of the cell and its two neighbours (brute-force scan)."""
+    rng = np.random.default_rng(12)
+    xi = np.linspace(0.0, 1.0, 201)
+    for trial in range(200):
+        q = rng.normal(size=24)
+        if trial % 3 == 0:
+            q = np.cumsum(np.abs(q))  # monotone data with kinks
+        qL, qR, dq, q6 = oracle.line_parabolas(q)
+        for c in range(2, 22):
+            vals = parabola_eval(qL[c], dq[c], q6[c], xi)
+            d = np.diff(vals)
+            tol = 1e-12 * (1.0 + np.max(np.abs(vals)))
+            assert np.all(d >= -tol) or np.all(d <= tol)
+            lo = min(q[c - 1], q[c], q[c + 1]) - tol
+            hi = max(q[c - 1], q[c], q[c + 1]) + tol
+            assert vals.min() >= lo and vals.max() <= hi
+
+
+def test_characteristic_averages_match_quadrature():
+    """Appendix, characteristic integrals: q_L(-lambda t) and q_R(lambda t) are the means
+    of eq. A1 over the right / left fraction y of the cell (independent quadrature)."""
+    rng = np.random.default_rng(13)
+    for _ in range(200):
+        qL, dq, q6 = rng.normal(size=3)
+        y = rng.uniform(0.0, 1.0)
+        qR = qL + dq
+        right = quad(lambda x: parabola_eval(qL, dq, q6, x), 1.0 - y, 1.0) / y
+        left = quad(lambda x: parabola_eval(qL, dq, q6, x), 0.0, y) / y
+        assert oracle.avg_right_part(qR, dq, q6, y) == pytest.approx(right, rel=1e-12, abs=1e-12)
+        assert oracle.avg_left_part(qL, dq, q6, y) == pytest.approx(left, rel=1e-12, abs=1e-12)
+
+
+# --------------------------------------------------------------- face Riemann (S2)
+
+def test_riemann_equal_states():
+    V, P = oracle.face_riemann(1.3, 1.3, 0.7, 0.7, 0.25, 0.25, 0.7, 0.7, 1.4)
+    assert V == 0.25 and P == 0.7
+
+
+def test_riemann_mirror_symmetry():
+    """Swapping left and right and negating velocities negates V and keeps P."""
+    rng = np.random.default_rng(14)
+    for _ in range(100):
+        rl, rr, pl, pr = rng.uniform(0.1, 5, 4)
+        vl, vr = rng.normal(size=2)
+        pls, prs = rng.uniform(0.1, 5, 2)
+        V1, P1 = oracle.face_riemann(rl, rr, pl, pr, vl, vr, pls, prs, 1.4)
+        V2, P2 = oracle.face_riemann(rr, rl, pr, pl, -vr, -vl, prs, pls, 1.4)
+        assert V2 == pytest.approx(-V1, rel=1e-13, abs=1e-13)
+        assert P2 == pytest.approx(P1, rel=1e-13)
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_riemann_weak_waves_match_exact_star_state(gamma):
+    """With piecewise-constant data the face solution is the acoustic (linearised)
+    Riemann solution; for weak jumps of size eps it must agree with the exact star state
+    to O(eps^2).  A missing impedance factor or a flipped sign is O(eps) and fails."""
+    rng = np.random.default_rng(15)
+    for _ in range(20):
+        r0, p0 = rng.uniform(0.5, 2.0, 2)
+        v0 = rng.normal()
+        dr, dp, dv = rng.normal(size=3)
+        errs = []
+        for eps in (1e-2, 5e-3):
+            rl, rr = r0 * (1 + eps * dr), r0 * (1 - eps * dr)
+            pl, pr = p0 * (1 + eps * dp), p0 * (1 - eps * dp)
+            vl, vr = v0 + eps * dv, v0 - eps * dv
+            V, P = oracle.face_riemann(rl, rr, pl, pr, vl, vr, pl, pr, gamma)
+            ps, us = exact.riemann_star(rl, vl, pl, rr, vr, pr, gamma)
+            errs.append(max(abs(P - ps) / p0, abs(V - us) / math.sqrt(gamma * p0 / r0)))
+        jump = 2e-2 * max(abs(dr), abs(dp), abs(dv), 0.1)
+        assert errs[0] < 0.5 * jump ** 2 + 1e-12  # an O(eps) mistake is ~jump
+        assert errs[1] < errs[0] * 0.35  # second order: halving eps quarters the error
+
+
+def test_face_lambda_between_cell_sound_speeds():
+    """The modified Roe average keeps lambda between the adjacent sound speeds, and at a
+    dense/rarefied interface stays near the dense side's speed (Sec. 1.1 remark)."""
+    rng = np.random.default_rng(16)
+    g = 1.4
+    for _ in range(200):
+        rl, rr, pl, pr = np.exp(rng.uniform(-8, 3, 4))
+        lam = oracle.face_lambda(rl, rr, pl, pr, g)
+        cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+        assert min(cl, cr) * (1 - 1e-12) <= lam <= max(cl, cr) * (1 + 1e-12)
+    # isothermal dense gas next to a 1e-8 rarer gas: lambda ~ the common sound speed
+    lam = oracle.face_lambda(1.0, 1e-8, 1.0, 1e-8, 1.0)
+    assert lam == pytest.approx(1.0, rel=1e-10)
+
+
+# ------------------------------------------------------------- energy correction
+
+def test_energy_correction_branches():
+    """Sec. 'The conservation of total energy': the four cases of the correction."""
+    # dense: rho eps = rho E - |m|^2 / (2 rho)
+    u, code = oracle.energy_correction([2.0, 1.0, -2.0, 0.5, 5.0, 9.0], 1e-5)
+    assert code == 0 and u[5] == pytest.approx(5.0 - (1 + 4 + 0.25) / 4.0)
+    assert np.all(u[:5] == [2.0, 1.0, -2.0, 0.5, 5.0])
+    # dense with non-positive difference: advected rho eps kept
+    u, code = oracle.energy_correction([1.0, 3.0, 0.0, 0.0, 1.0, 0.25], 1e-5)
+    assert code == 2 and u[5] == 0.25
+    # vacuum: keep eps and direction, |v| = sqrt(2 (E - eps)) per unit mass
+    rho = 1e-9
+    u, code = oracle.energy_correction([rho, 3e-9, 4e-9, 0.0, 5e-9, 1e-9], 1e-5)
+    v = np.array(u[1:4]) / rho
+    assert code == 1 and u[5] == 1e-9
+    assert np.linalg.norm(v) == pytest.approx(math.sqrt(2 * (5e-9 - 1e-9) / rho), rel=1e-13)
+    assert v[0] / v[1] == pytest.approx(0.75, rel=1e-13)
+    # vacuum with rho E < rho eps: momentum dropped, rho eps = rho E
+    u, code = oracle.energy_correction([rho, 3e-9, 4e-9, 0.0, 1e-9, 2e-9], 1e-5)
+    assert code == 3 and np.all(u[1:4] == 0.0) and u[5] == 1e-9
+
+
+# ----------------------------------------------------------------- whole step
+
+def test_cfl_closed_form():
+    pb = inputs.uniform_flow(n=(8, 6, 5), v=(0.3, -0.4, 1.2), rho=2.0, p=3.0)
+    g = grid_of(pb)
+    dt = oracle.cfl_dt(g, pb.u)
+    c = math.sqrt(1.4 * 3.0 / 2.0)
+    vmag = math.sqrt(0.09 + 0.16 + 1.44)
+    assert dt == pytest.approx(0.2 * min(pb.h) / (vmag + c), rel=1e-14)
+
+
+def test_uniform_flow_unchanged():
+    """Galilean uniform flow: flat parabolas, equal fluxes, nothing changes."""
+    pb = inputs.uniform_flow()
+    g = grid_of(pb)
+    u = pb.u
+    for _ in range(3):
+        u, dg = oracle.step(g, u, oracle.cfl_dt(g, u))
+    for a, b in zip(u, pb.u):
+        assert np.max(np.abs(a - b)) <= 1e-14 * max(1.0, np.max(np.abs(b)))
+
+
+def test_conservation_periodic_random():
+    """Periodic box: mass, momentum and total energy are conserved to round-off (both
+    stages are in flux form; a lost or doubled face term breaks this)."""
+    pb = inputs.random_smooth(n=(12, 10, 8))
+    g = grid_of(pb)
+    s0 = oracle.diagnostics(g, pb.u)["sums"]
+    u = pb.u
+    for _ in range(4):
+        u, dg = oracle.step(g, u, oracle.cfl_dt(g, u))
+    assert dg["n_vacuum"] == 0
+    for f in range(5):
+        scale = max(abs(s0[0]), abs(s0[4]))
+        assert abs(dg["sums"][f] - s0[f]) <= 2e-14 * scale
+
+
+def test_conservation_rough_data():
+    pb = inputs.random_rough(n=(10, 9, 8), bc=(1,) * 6)
+    g = grid_of(pb)
+    s0 = oracle.diagnostics(g, pb.u)["sums"]
+    u, dg = oracle.step(g, pb.u, 0.5 * oracle.cfl_dt(g, pb.u))
+    for f in range(5):
+        assert abs(dg["sums"][f] - s0[f]) <= 1e-13 * max(abs(s0[0]), abs(s0[4]))
+
+
+def test_planar_data_stays_planar_and_matches_1d():
+    """Data uniform in y and z stays bitwise uniform and equals the 1D run."""
+    n = 32
+    p3 = inputs.planar_sod_3d(n)
+    p3.u = [a[:6, :5, :].copy() for a in p3.u]
+    p3.n = (n, 5, 6)
+    g3 = grid_of(p3)
+    p1 = inputs.sod_1d(n, cfl=0.2)
+    g1 = grid_of(p1)
+    u3, u1 = p3.u, p1.u
+    for _ in range(10):
+        tau = oracle.cfl_dt(g1, u1)
+        u3, _ = oracle.step(g3, u3, tau)
+        u1, _ = oracle.step(g1, u1, tau)
+    for f in range(6):
+        assert np.all(u3[f] == u3[f][:1, :1, :])
+    for f in (0, 1, 4, 5):
+        d = np.abs(u3[f][0, 0] - u1[f][0, 0]).sum() / max(np.abs(u1[f]).sum(), 1e-300)
+        assert d <= 1e-12
+
+
+def test_point_blast_mirror_and_permutation_symmetry():
+    """A blast centred in the box is symmetric under x -> -x and under axis exchange."""
+    pb = inputs.point_blast_3d(n=16)
+    g = grid_of(pb)
+    u = pb.u
+    for _ in range(6):
+        u, dg = oracle.step(g, u, oracle.cfl_dt(g, u))
+    rho, mx, my, mz, en, ei = u
+    scale = np.max(np.abs(en))
+    assert np.max(np.abs(rho - rho[:, :, ::-1])) <= 1e-12 * np.max(rho)
+    assert np.max(np.abs(mx + mx[:, :, ::-1])) <= 1e-12 * np.max(np.abs(mx))
+    assert np.max(np.abs(en - en[::-1, :, :])) <= 1e-12 * scale
+    assert np.max(np.abs(rho - np.transpose(rho, (0, 2, 1)))) <= 1e-12 * np.max(rho)
+    assert np.max(np.abs(mx - np.transpose(my, (0, 2, 1)))) <= 1e-12 * np.max(np.abs(mx))
+    assert np.max(np.abs(rho - np.transpose(rho, (2, 1, 0)))) <= 1e-12 * np.max(rho)
+
+
+def _sod_l1(n, row=1):
+    pb = inputs.sod_1d(n, row=row)
+    g = grid_of(pb)
+    u, t, steps, dg = oracle.run(g, pb.u, pb.t_end)
+    edges = np.arange(n + 1) / n
+    ex = exact.riemann_cell_averages(*pb.extra["states"], pb.gamma, pb.extra["x_split"], t,
+                                     edges, sub=8)
+    return np.mean(np.abs(u[0].ravel() - ex[0])), u, dg
+
+
+def test_sod_converges_to_exact_solution():
+    """Table 2 row 1 against the exact Riemann solution: L1(rho) falls under refinement,
+    and at 256 cells stays below the bound registered from the first oracle run
+    (2.55e-3 measured; bound 3.5e-3)."""
+    e100, _, _ = _sod_l1(100)
+    e200, _, _ = _sod_l1(200)
+    e256, u, dg = _sod_l1(256)
+    assert e200 < 0.7 * e100
+    assert e256 < 3.5e-3
+    assert dg["n_nonphys"] == 0
+    # conserved to round-off: the boundary states stay static, the momentum gain is
+    # exactly (p_L - p_R) t
+    assert dg["sums"][0] == pytest.approx(0.5625, rel=1e-14)
+    assert dg["sums"][4] == pytest.approx(1.375, rel=1e-14)
+    assert dg["sums"][1] == pytest.approx(0.9 * 0.2, rel=1e-12)
+
+
+@pytest.mark.parametrize("row", [2, 3])
+def test_table2_rows_2_3_positive_and_close(row):
+    """Rows 2 (strong rarefactions) and 3 (pressure ratio 1e5) stay physical and close to
+    the exact solution in L1."""
+    e, u, dg = _sod_l1(256, row=row)
+    assert dg["n_nonphys"] == 0
+    scale = {2: 0.05, 3: 0.12}[row]
+    assert e < scale
+
+
+def test_sod_shock_width_two_to_three_cells():
+    """Sec. 'The Sod shock-tube problem': the high-order shock spans about two cells
+    (100 cells, t = 0.2).  Measured as the 10-90% rise of rho across the shock."""
+    n = GOLDEN["shock_tubes"]["cells"]
+    pb = inputs.sod_1d(n)
+    g = grid_of(pb)
+    u, t, steps, dg = oracle.run(g, pb.u, pb.t_end)
+    rho = u[0].ravel()
+    ps, us = exact.riemann_star(*pb.extra["states"], pb.gamma)
+    # post-shock density from the exact solution
+    r_post = exact.riemann_sample(*pb.extra["states"], pb.gamma, np.array([us + 1e-9]))[0][0]
+    lo, hi = 0.125, r_post
+    x = (np.arange(n) + 0.5) / n
+    window = (x > 0.75) & (x < 0.95)
+    r = rho[window]
+    f = (r - lo) / (hi - lo)
+    width = np.sum((f > 0.1) & (f < 0.9))
+    assert width <= GOLDEN["shock_width_cells"]["high_order"] + 1
+
+
+def _advected_error(n):
+    pb = inputs.advected_wave(n)
+    g = grid_of(pb)
+    u, t, steps, dg = oracle.run(g, pb.u, 1.0)
+    ex = exact.advected_wave_exact(pb.extra["edges"], t)
+    return np.mean(np.abs(u[0].ravel() - ex))
+
+
+def test_advected_wave_order():
+    """Smooth density wave advected one period (exact = translation): L1 order >= 1.5."""
+    e32, e64 = _advected_error(32), _advected_error(64)
+    order = math.log2(e32 / e64)
+    assert order >= 1.5, order
+
+
+def test_aksenov_order():
+    """Sec. 'The Aksenov Test': T = log2(E_{N/2}/E_N) on density at N = 628, t = pi/2,
+    at the paper's CFL = 0.2.  The paper prints T = 1.713.  The scheme as the paper states
+    it advances the Eulerian and Lagrangian stages one after the other with forward
+    differences in time (its conclusion calls the time discretisation simple), so with
+    tau proportional to h its error is O(tau) = O(h): the oracle measures T = 1.08 and the
+    error halves when CFL halves at fixed N (checked below).  The pin is therefore first
+    order, 0.9 <= T <= 1.3, plus the O(tau) signature; the paper's 1.713 is recorded as
+    not reproduced.  A dropped or mis-signed term stops convergence (T ~ 0) or blows up."""
+    errs = {}
+    for n, cfl in ((314, 0.2), (628, 0.2), (314, 0.1)):
+        pb = inputs.aksenov(n, cfl=cfl)
+        g = grid_of(pb)
+        u, t, steps, dg = oracle.run(g, pb.u, pb.t_end)
+        rho_ex, _ = exact.aksenov_cell_averages(pb.extra["edges"], t)
+        errs[(n, cfl)] = np.sum(np.abs(u[0].ravel() - rho_ex)) * pb.h[0]
+    T = math.log2(errs[(314, 0.2)] / errs[(628, 0.2)])
+    assert 0.9 <= T <= 1.3, (T, errs)
+    assert errs[(314, 0.1)] < 0.75 * errs[(314, 0.2)]
+    assert errs[(628, 0.2)] < 3e-3
+
+
+def test_acoustic_wave_first_order_in_time_high_order_in_space():
+    """Small-amplitude sound wave, one period.  Pure advection (test_advected_wave_order)
+    converges at order > 2; acoustics couples both stages and converges at first order
+    with an error proportional to CFL, the splitting's signature."""
+    def err(n, cfl, eps=1e-6, g=1.4):
+        h = 1.0 / n
+        edges = np.arange(n + 1) * h
+        k = 2 * math.pi
+        avg = (np.cos(k * edges[:-1]) - np.cos(k * edges[1:])) / (k * h)
+        c = math.sqrt(g)
+        u = inputs.conserved((1 + eps * avg)[None, None, :], (c * eps * avg)[None, None, :], 0.0,
+                             0.0, (1 + g * eps * avg)[None, None, :], g)
+        G = oracle.Grid((n, 1, 1), (h, 1.0, 1.0), g, (1, 1, 0, 0, 0, 0), cfl, rho_mean=1.0)
+        out, t, steps, dg = oracle.run(G, u, 1.0 / c)
+        return np.mean(np.abs(out[0].ravel() - (1 + eps * avg))) / eps
+    e32, e64, e32h = err(32, 0.4), err(64, 0.4), err(32, 0.2)
+    assert 0.85 <= math.log2(e32 / e64) <= 1.3
+    assert 0.4 <= e32h / e32 <= 0.65
+
+
+def test_vacuum_expansion_conserves_total_energy():
+    """Sec. 'The expansion of gas into vacuum': total energy constant to round-off while
+    kinetic energy rises and internal energy falls.  The printed scheme survives a density
+    contrast of 1e-2 but not 1e-3 (the acoustic face solve, with one impedance from the
+    dense side, pushes a nearly empty cell with about half the dense pressure), so the
+    ambient gas is at 1e-2 and the vacuum threshold is raised to 0.3 x mean density so
+    that the vacuum branch of the energy correction runs."""
+    pb = inputs.vacuum_sphere(n=20, rho_vac=1e-2, p_vac=1e-2)
+    pb.bc = (1,) * 6  # periodic: nothing leaves the box
+    g = grid_of(pb)
+    g.vacuum_frac = 0.3
+    u = pb.u
+    d0 = oracle.diagnostics(g, u)
+    kin = []
+    nvac = 0
+    for _ in range(12):
+        u, dg = oracle.step(g, u, oracle.cfl_dt(g, u))
+        nvac += dg["n_vacuum"]
+        kin.append(np.sum((u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / (2 * u[0])))
+    assert nvac > 0 and dg["n_nonphys"] == 0
+    # 12 steps of 8000 cells: round-off of the sums, ~1e-14 relative per step
+    assert abs(dg["sums"][4] - d0["sums"][4]) <= 1e-12 * d0["sums"][4]
+    assert dg["sums"][0] == pytest.approx(d0["sums"][0], rel=1e-12)
+    assert kin[-1] > kin[0] > 0
+    assert dg["sums"][5] < d0["sums"][5]
+
+
+@pytest.mark.slow
+def test_point_blast_radius_matches_sedov():
+    """Point blast (Sec. 'The Sedov blast wave' setup with gamma = 5/3): the radius of the
+    density peak follows R = xi0 (E t^2/rho0)^(1/5) within two cells, xi0 from the
+    self-similar solution."""
+    n = 32
+    xi0 = exact.sedov_xi0(5.0 / 3.0)
+    pb = inputs.point_blast_3d(n=n, radius_end=0.3, xi0=xi0)
+    g = grid_of(pb)
+    u, t, steps, dg = oracle.run(g, pb.u, pb.t_end)
+    h = pb.h[0]
+    c = (np.arange(n) + 0.5) * h - 0.5
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z).ravel()
+    rho = u[0].ravel()
+    bins = np.arange(0, 0.5, h)
+    idx = np.digitize(r, bins)
+    prof = np.array([rho[idx == i].mean() if np.any(idx == i) else 0 for i in range(1, len(bins))])
+    r_peak = bins[np.argmax(prof)] + 0.5 * h
+    R = xi0 * (1.0 * t * t / 1.0) ** 0.2
+    assert abs(r_peak - R) <= 2.0 * h, (r_peak, R)
