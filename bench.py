@@ -1,0 +1,296 @@
+"""Throughput of the PPML step on GB300: Mcell-updates/s, FP32 (headline) and FP64.
+
+Workload: 3D point blast, 256^3 cells on [-0.5, 0.5]^3, gamma = 5/3, rho = 1, p = 1e-5,
+E = 1 in the 8 central cells, outflow, CFL 0.2 (synthetic, seeded; no dataset).  One
+step = Eulerian stage + Lagrangian stage + energy correction + CFL step + FP64 sums, all
+in libppml.so through its C ABI.  The state (6 x 67 MB in FP32) is far larger than L2,
+so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ppml|reference]
+Under torchrun with N > 1 each rank advances its own replica (the grid is not split
+across GPUs); value = all ranks' cell-updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PPML Mcell-updates/s per step, FP32 vs FP64, and % of GB300 HBM roofline"
+N_CELLS_SIDE = 256
+# algorithmic bytes per cell per step (FP32 state): Eulerian reads 6 fields, writes 5;
+# Lagrangian reads 6, writes 6.  FP64 doubles them.
+BYTES_EUL = {4: 44, 8: 88}
+BYTES_LAG = {4: 48, 8: 96}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload_steps=1, max_seconds=30.0):
+    """The FP64 oracle (as it stands) on the host cores: steps of the same 256^3 point
+    blast, bounded in time.  Returns (Mcell-updates/s, cores, sample description)."""
+    import oracle
+    from paper_1607_01105_gb300 import inputs
+    pb = inputs.point_blast_3d(N_CELLS_SIDE)
+    g = oracle.Grid(pb.n, pb.h, pb.gamma, pb.bc, pb.cfl, rho_mean=oracle.mean_density(pb.u))
+    u = pb.u
+    dt = oracle.cfl_dt(g, u)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < workload_steps:
+        u, dg = oracle.step(g, u, dt)
+        dt = dg["dt_cfl"]
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pb.cells * steps / el / 1e6, cores, f"{steps} oracle step(s) of the 256^3 point blast from t=0", el
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(1)
+    t0 = time.perf_counter()
+    tot_cells = 0
+    for _ in range(args.steps):
+        v, cores, sample, el = cpu_baseline(1)
+        vals.append(el)
+        tot_cells += N_CELLS_SIDE ** 3
+    el = time.perf_counter() - t0
+    value = tot_cells / el / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "point_blast_3d 256^3, gamma=5/3, CFL 0.2, outflow",
+                       "global_batch": 1, "seq_len": 0, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
+                             "unit": "Mcell-updates/s",
+                             "sample": f"{args.steps} timed oracle steps of the 256^3 point blast"},
+            "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ppml", choices=["ppml", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1607_01105_gb300 import inputs, ppml
+
+    pb = inputs.point_blast_3d(args.n)
+    cells = pb.cells
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for dtype, name in ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64")):
+        elt = 4 if dtype == ppml.PPML_F32 else 8
+        u = ppml.to_device(pb.u, dtype)
+        v = [torch.empty_like(x) for x in u]
+        grid = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u)
+        steps = args.steps if dtype == ppml.PPML_F32 else max(3, args.steps // 10)
+        for _ in range(args.warmup):
+            grid.step(u, v, 0.0)
+            u, v = v, u
+        barrier()
+        grid.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as cs:
+            barrier()
+            ev0.record(stream)
+            for _ in range(steps):
+                grid.step(u, v, 0.0)
+                u, v = v, u
+            ev1.record(stream)
+            barrier()
+        ms = ev0.elapsed_time(ev1)
+        kms, ksteps = grid.kernel_times()
+        grid.profile(False)
+        d = grid.diag(raise_nonphysical=False)
+        ms = max_over_ranks(ms)
+        results[name] = {"ms": ms, "steps": steps, "kernel_ms": [x / ksteps for x in kms],
+                         "clocks": cs.summary(), "elt": elt, "diag": d}
+        # end to end through host buffers (FP32 headline only): pinned H2D of the input
+        # state, the step, D2H of the new state, every step inside the timed region
+        if dtype == ppml.PPML_F32:
+            hin = [x.cpu().pin_memory() for x in u]
+            hout = [torch.empty_like(x) for x in hin]
+            e_steps = max(3, steps // 5)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e_steps):
+                for dst, src in zip(u, hin):
+                    dst.copy_(src, non_blocking=True)
+                grid.step(u, v, 0.0)
+                for dst, src in zip(hout, v):
+                    dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            barrier()
+            ems = max_over_ranks(e0.elapsed_time(e1))
+            results["e2e"] = {"ms": ems, "steps": e_steps,
+                              "h2d": 6 * cells * elt, "d2h": 6 * cells * elt}
+        grid.close()
+        del u, v
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        peak, peak_kind = load_peaks()
+        r32, r64 = results["f32"], results["f64"]
+        value = world * cells * r32["steps"] / (r32["ms"] * 1e-3) / 1e6
+        v64 = world * cells * r64["steps"] / (r64["ms"] * 1e-3) / 1e6
+        keul, klag, kfin = r32["kernel_ms"]
+        dom = "lagrangian" if klag >= keul else "eulerian"
+        kms = max(klag, keul)
+        algo_bytes = (BYTES_LAG if dom == "lagrangian" else BYTES_EUL)[4] * cells
+        achieved = algo_bytes / (kms * 1e-3) / 1e9
+        step_bytes = (BYTES_EUL[4] + BYTES_LAG[4]) * cells
+        e2e = results["e2e"]
+        e2e_val = world * cells * e2e["steps"] / (e2e["ms"] * 1e-3) / 1e6
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+            "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"] / r32["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"point_blast_3d {args.n}^3, gamma=5/3, rho=1, p=1e-5, E=1 in "
+                                   f"the 8 central cells, CFL 0.2, outflow; FP32 state, FP64 "
+                                   f"dt/sums/energy correction",
+                       "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "no flush: state 403 MB x 2 + U* 336 MB > 129 MB L2"},
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_kernel<float>",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_cell": (BYTES_LAG if dom == "lagrangian" else BYTES_EUL)[4],
+                         "kernel_ms": {"eulerian": keul, "lagrangian": klag, "finalize": kfin},
+                         "step_hbm_frac": step_bytes / (r32["ms"] / r32["steps"] * 1e-3) / 1e9 / peak},
+            "fp64": {"value": v64, "unit": "Mcell-updates/s", "ms_per_step": r64["ms"] / r64["steps"],
+                     "steps": r64["steps"], "kernel_ms": r64["kernel_ms"]},
+            "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": 3 * r32["steps"],
+            "clocks": r32["clocks"],
+            "clocks_fp64": r64["clocks"],
+        }
+        if not args.no_cpu_baseline:
+            cv, cores, sample, el = cpu_baseline(1)
+            line["cpu_baseline"] = {"value": cv, "unit": "Mcell-updates/s", "cores": cores,
+                                    "kind": "oracle", "sample": sample, "seconds": el}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

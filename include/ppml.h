@@ -1,0 +1,175 @@
+/*
+ * ppml.h -- C ABI of libppml.so, a GB300 (sm_103a) implementation of one timestep of
+ * the PPML operator-splitting Godunov scheme of Kulikov & Vorobyov (arXiv:1607.01105)
+ * for the ideal-gas Euler equations with total and internal energy on a uniform grid.
+ *
+ * What a step computes (paper Sec. 1 "NUMERICAL SCHEME" and the Appendix):
+ *   Eulerian stage (Sec. 1.1/1.2, eqs. SCHdensEulerian..SCHintenEulerian,
+ *     lowriemannvelocity, lowriemannpressure): PPML parabolas of v and p per cell and
+ *     axis (Appendix Steps 1-3), the acoustic Riemann solution (V, P) at every face with
+ *     the modified Roe averages, and the update rho v -= tau dP/dx, rho E -= tau d(PV)/dx,
+ *     rho eps -= tau (gamma-1) rho eps dV/dx summed over the three axes;
+ *   Lagrangian stage (Sec. 1.3, eqs. genlagrange, fluxonlagrangestage,
+ *     modspaceaveragevelocitylagrange, veltemplate): the 9-point transverse velocity
+ *     template, Roe-weighted face velocity, upwind parabola-average fluxes of rho, rho v,
+ *     rho E, rho eps, unsplit update;
+ *   energy consistency (Sec. 1.4), the CFL step of the new state (Sec. 1.1) and FP64
+ *     conservation sums.
+ *
+ * Conventions shared by every call:
+ *   - State: six device arrays (rho, m_x, m_y, m_z, rho E, rho eps), each nx*ny*nz
+ *     interior cells, x fastest, contiguous, element type per ppml_grid_desc.dtype,
+ *     16-byte aligned.  No ghost cells: the boundary conditions are applied when the
+ *     kernels read neighbours (outflow = zero-gradient, periodic = wrap, reflecting =
+ *     mirror with the normal momentum negated; edges and corners as if ghosts were
+ *     filled along x, then y, then z).
+ *   - The caller owns every state array and the stream; the library owns its handle,
+ *     the intermediate state U* and its reduction scratch (allocated by ppml_init_grid
+ *     with cudaMalloc, freed by ppml_free_grid).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous
+ *     on that stream unless they return a host value (documented per call).
+ *   - Return value: PPML_OK (0) or an error code; ppml_last_error() gives a message for
+ *     the calling thread.  No call aborts, prints or exits.
+ *   - Not thread-safe per handle: one handle must not be used from two host threads at
+ *     once.  Different handles are independent.
+ */
+#ifndef PPML_H
+#define PPML_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PPML_OK = 0,
+  PPML_E_INVAL = 1,       /* bad argument: sizes, gamma, cfl, null or misaligned pointers */
+  PPML_E_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+  PPML_E_NONPHYSICAL = 3, /* reported by ppml_read_diag: rho <= 0, rho eps <= 0 or NaN seen */
+  PPML_E_TIMEOUT = 4,     /* reserved: no call waits on another kernel */
+  PPML_E_NOMEM = 5        /* device or host allocation failed */
+} ppml_status;
+
+typedef enum {
+  PPML_F32 = 0, /* state in float; dt, conservation sums and the energy correction in double */
+  PPML_F64 = 1  /* everything in double */
+} ppml_dtype;
+
+typedef enum { PPML_BC_OUTFLOW = 0, PPML_BC_PERIODIC = 1, PPML_BC_REFLECT = 2 } ppml_bc;
+
+/* flag bits accumulated on the device (ppml_diag.flags) */
+#define PPML_FLAG_NONPHYSICAL 1u /* an output cell had rho <= 0, rho eps <= 0 or a NaN/Inf */
+#define PPML_FLAG_DT_ZERO 2u     /* the CFL step underflowed to 0 (or t_end reached) */
+
+/* Problem statement (paper Sec. 1 and Sec. 1.1: grid, gamma, CFL number, boundaries). */
+typedef struct {
+  int nx, ny, nz;     /* interior cells per axis, >= 1; an axis with one cell is inactive */
+  double h[3];        /* cell size per axis (> 0); cell volume h[0]*h[1]*h[2] */
+  double gamma;       /* ratio of specific heats, > 1 */
+  double cfl;         /* Courant number, 0 < cfl < 1 (paper: 0.2) */
+  int bc[6];          /* ppml_bc per face: -x, +x, -y, +y, -z, +z; periodic faces come in
+                         pairs; an inactive axis may not be reflecting */
+  int dtype;          /* ppml_dtype */
+  double vacuum_frac; /* vacuum threshold of the energy correction relative to the mean
+                         initial density (paper Sec. 1.4: five orders of magnitude, 1e-5);
+                         <= 0 selects 1e-5 */
+  double t_end;       /* > 0: the device-side CFL step is clipped so t lands on t_end */
+} ppml_grid_desc;
+
+/* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions). */
+typedef struct {
+  void* f[6];
+} ppml_state;
+
+/* Host copy of the device-resident diagnostics after the last step or dt call. */
+typedef struct {
+  double t;          /* simulated time reached */
+  double dt_next;    /* CFL step of the last output state, clipped to t_end */
+  double vmax, cmax; /* max |v| and max sound speed of that state */
+  double sums[6];    /* sum over cells of each field times the cell volume (FP64) */
+  long long steps;   /* steps taken since init */
+  long long n_vacuum;/* cells that took the vacuum branch of the energy correction, last step */
+  long long n_bad;   /* cells flagged non-physical in the last diagnosed state */
+  unsigned flags;    /* PPML_FLAG_* bits raised since init */
+} ppml_diag;
+
+typedef struct ppml_grid ppml_grid;
+
+/* Create a handle for the grid in *d and allocate its scratch (U*: five fields of the
+ * state's type; reduction partials).  Reads u0 once on `stream` to fix the mean initial
+ * density (the vacuum threshold reference, Sec. 1.4) and the first CFL step; synchronizes
+ * the stream.  u0 is not modified.  On error *out is NULL. */
+int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, void* stream, ppml_grid** out);
+
+/* Free the handle and its scratch (synchronizes the device first).  NULL is a no-op. */
+int ppml_free_grid(ppml_grid* g);
+
+/* CFL step of state u (Sec. 1.1: tau = cfl * min_a h_a / (max|v| + max c), the maxima
+ * taken separately, |v| Euclidean, inactive axes excluded), clipped to t_end - t.  The
+ * result is stored on the device (ppml_dt_device) for the next ppml_step with dt <= 0;
+ * if dt_host is non-NULL the stream is synchronized and the value copied there. */
+int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, void* stream);
+
+/* One full step U^n -> U^{n+1} (Eulerian stage, Lagrangian stage, energy correction),
+ * with the CFL step and the FP64 sums of U^{n+1} computed in the same pass.
+ * dt > 0: use it; dt <= 0: use the device-resident step from ppml_cfl_dt or from the
+ * previous ppml_step (no host synchronization, so steps can be captured in a CUDA graph).
+ * u_in and u_out must not alias; u_in is not modified.  Asynchronous. */
+int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, double dt, void* stream);
+
+/* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated) into
+ * u_star.  For stage-level checks; same dt convention as ppml_step; does not advance t. */
+int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star, double dt,
+                        void* stream);
+
+/* FP64 sums of each field of u times the cell volume.  Synchronizes the stream. */
+int ppml_conserved_sums(ppml_grid* g, const ppml_state* u, double out[6], void* stream);
+
+/* Copy the device-resident diagnostics to the host.  Synchronizes the stream.  Returns
+ * PPML_E_NONPHYSICAL (with *out filled) if PPML_FLAG_NONPHYSICAL is set. */
+int ppml_read_diag(ppml_grid* g, ppml_diag* out, void* stream);
+
+/* Device address of the handle's current step size (one double). */
+const double* ppml_dt_device(const ppml_grid* g);
+
+/* Measurement hook (not part of the paper's method).  enable != 0: every following
+ * ppml_step records CUDA events on its stream around each of its kernels (Eulerian,
+ * Lagrangian, finalize) and accumulates their durations; enable == 0 stops recording.
+ * Do not enable while capturing a CUDA graph.  Resets the accumulated times. */
+int ppml_profile(ppml_grid* g, int enable);
+
+/* Accumulated kernel durations in milliseconds (ms[0] Eulerian, ms[1] Lagrangian,
+ * ms[2] finalize) and the number of profiled steps.  Synchronizes the device. */
+int ppml_kernel_times(ppml_grid* g, double ms[3], long long* steps);
+
+/* ---------------------------------------------------------------- batched 1D problems
+ * Many independent 1D problems of uneven lengths (outflow boundaries, gamma shared),
+ * advanced by one persistent launch per call.  Each instance keeps its own time, CFL
+ * step and end time.  Packed layout: four device arrays (rho, m, rho E, rho eps) of
+ * sum(ncells) elements of the batch's type, instance i at [offset_i, offset_i + n_i). */
+typedef struct ppml_batch ppml_batch;
+
+/* ncells[n_inst] (each >= 4), h[n_inst] (> 0), t_end[n_inst] (> 0) are host arrays;
+ * they are copied.  vacuum_frac <= 0 selects 1e-5 (reference: each instance's own mean
+ * initial density, computed at the first ppml_batch_step). */
+int ppml_batch_init(int n_inst, const int* ncells, const double* h, const double* t_end,
+                    double gamma, double cfl, double vacuum_frac, int dtype, ppml_batch** out);
+
+/* Advance every unfinished instance by up to max_steps steps (each instance stops at its
+ * t_end) in one launch.  state: four device pointers (see layout), updated in place.
+ * If done_host is non-NULL the stream is synchronized and the number of finished
+ * instances written there. */
+int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* done_host,
+                    void* stream);
+
+/* Per-instance time reached and steps taken (host arrays of n_inst).  Synchronizes. */
+int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream);
+
+int ppml_batch_free(ppml_batch* b);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* ppml_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPML_H */

@@ -164,6 +164,14 @@ static void fill_ghosts(const gshape* s, const oracle_desc* d, double* q, int fi
   }
 }
 
+/* The two axes transverse to a, ordered (inner, outer) by memory stride, so that threads
+ * splitting the outer axis write disjoint planes or rows (no false sharing). */
+static void transverse(int a, int* inner, int* outer) {
+  int b = (a + 1) % 3, c = (a + 2) % 3;
+  *inner = b < c ? b : c;
+  *outer = b < c ? c : b;
+}
+
 /* ---------------------------------------------------------------- PPML parabolas */
 
 /* Appendix, Step 1: limited slope delta_m q_i of a cell from its two neighbours. */
@@ -289,7 +297,8 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
   }
   for (int a = 0; a < 3; a++) {
     if (s->n[a] == 1) continue; /* a single cell along an axis gives exactly zero fluxes */
-    int b = (a + 1) % 3, cax = (a + 2) % 3;
+    int b, cax;
+    transverse(a, &b, &cax);
     size_t st = axis_stride(s, a);
     int N = s->N[a];
     double rk = tau / d->h[a];
@@ -297,7 +306,7 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
     {
       linebuf lb;
       lb_alloc(&lb, N);
-#pragma omp for collapse(2) schedule(static)
+#pragma omp for schedule(static)
       for (int ic = NG; ic < NG + s->n[cax]; ic++)
         for (int ib = NG; ib < NG + s->n[b]; ib++) {
           int idx[3];
@@ -332,7 +341,7 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
     }
   }
   /* S3 update of the interior */
-#pragma omp parallel for collapse(2) schedule(static)
+#pragma omp parallel for schedule(static)
   for (int k = NG; k < NG + s->n[2]; k++)
     for (int j = NG; j < NG + s->n[1]; j++)
       for (int i = NG; i < NG + s->n[0]; i++) {
@@ -378,7 +387,9 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
 
   for (int a = 0; a < 3; a++) {
     if (s->n[a] == 1) continue;
-    int b = (a + 1) % 3, cax = (a + 2) % 3;
+    int b = (a + 1) % 3, cax = (a + 2) % 3; /* template roles (eq. veltemplate) */
+    int li, lo;                             /* loop order (memory strides) */
+    transverse(a, &li, &lo);
     size_t st = axis_stride(s, a), sb = axis_stride(s, b), sc = axis_stride(s, cax);
     int N = s->N[a];
     double rk = tau / d->h[a];
@@ -386,14 +397,16 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
     /* S5: 9-point template in the plane normal to a, on cells whose transverse
      * neighbours exist (single-cell transverse axes use the cell itself, which makes
      * the template reduce to the 1D / 2D marginals). */
-#pragma omp parallel for collapse(2) schedule(static)
-    for (int ic = 0; ic < s->N[cax]; ic++)
-      for (int ib = 0; ib < s->N[b]; ib++) {
+#pragma omp parallel for schedule(static)
+    for (int io = 0; io < s->N[lo]; io++)
+      for (int ii = 0; ii < s->N[li]; ii++) {
+        int idx[3];
+        idx[lo] = io; idx[li] = ii;
+        int ib = idx[b], ic = idx[cax];
         int bm = (s->n[b] == 1) ? 0 : 1, cm = (s->n[cax] == 1) ? 0 : 1;
         if (ib - bm < 0 || ib + bm >= s->N[b] || ic - cm < 0 || ic + cm >= s->N[cax]) continue;
         for (int ia = 0; ia < N; ia++) {
-          int idx[3];
-          idx[a] = ia; idx[b] = ib; idx[cax] = ic;
+          idx[a] = ia;
           size_t g = gidx(s, idx[0], idx[1], idx[2]);
           size_t db = sb * (size_t)bm, dc = sc * (size_t)cm;
           double corners = vel[g + db + dc] + vel[g + db - dc] + vel[g - db + dc] + vel[g - db - dc];
@@ -402,11 +415,11 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
         }
       }
     /* faces along a: v hat at c+1/2 for the interior lines */
-#pragma omp parallel for collapse(2) schedule(static)
-    for (int ic = NG; ic < NG + s->n[cax]; ic++)
-      for (int ib = NG; ib < NG + s->n[b]; ib++) {
+#pragma omp parallel for schedule(static)
+    for (int io = NG; io < NG + s->n[lo]; io++)
+      for (int ii = NG; ii < NG + s->n[li]; ii++) {
         int idx[3];
-        idx[a] = 0; idx[b] = ib; idx[cax] = ic;
+        idx[a] = 0; idx[lo] = io; idx[li] = ii;
         size_t base = gidx(s, idx[0], idx[1], idx[2]);
         for (int c = NG - 1; c <= NG + s->n[a] - 1; c++) {
           size_t gl = base + st * c, gr = gl + st;
@@ -419,11 +432,11 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
     {
       linebuf lb;
       lb_alloc(&lb, N);
-#pragma omp for collapse(2) schedule(static)
-      for (int ic = NG; ic < NG + s->n[cax]; ic++)
-        for (int ib = NG; ib < NG + s->n[b]; ib++) {
+#pragma omp for schedule(static)
+      for (int io = NG; io < NG + s->n[lo]; io++)
+        for (int ii = NG; ii < NG + s->n[li]; ii++) {
           int idx[3];
-          idx[a] = 0; idx[b] = ib; idx[cax] = ic;
+          idx[a] = 0; idx[lo] = io; idx[li] = ii;
           size_t base = gidx(s, idx[0], idx[1], idx[2]);
           for (int f = 0; f < NFIELD; f++) {
             for (int c = 0; c < N; c++) lb.q[c] = Us[f][base + st * c];
@@ -445,7 +458,7 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
       lb_free(&lb);
     }
   }
-#pragma omp parallel for collapse(2) schedule(static)
+#pragma omp parallel for schedule(static)
   for (int k = NG; k < NG + s->n[2]; k++)
     for (int j = NG; j < NG + s->n[1]; j++)
       for (int i = NG; i < NG + s->n[0]; i++) {

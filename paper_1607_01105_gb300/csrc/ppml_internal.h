@@ -1,0 +1,10 @@
+// Host-side helpers shared by the translation units of libppml.so.
+#pragma once
+#include <cuda_runtime.h>
+
+// Record a formatted message for ppml_last_error() on this thread and return `code`.
+int ppml_fail(int code, const char* fmt, ...);
+// Clear this thread's message (every public entry point starts with it).
+void ppml_clear_error();
+// Check cudaGetLastError() after a launch; returns PPML_OK or PPML_E_CUDA.
+int ppml_check_launch(const char* what);

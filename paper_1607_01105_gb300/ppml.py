@@ -1,0 +1,244 @@
+"""Thin ctypes binding of libppml.so (C ABI in include/ppml.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels.
+Device memory and streams come from PyTorch.  If the compiled library is missing this
+module raises at import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppml.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PPML_OK, PPML_E_INVAL, PPML_E_CUDA, PPML_E_NONPHYSICAL, PPML_E_TIMEOUT, PPML_E_NOMEM = range(6)
+PPML_F32, PPML_F64 = 0, 1
+OUTFLOW, PERIODIC, REFLECT = 0, 1, 2
+FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
+EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppml_eulerian_stage",
+            "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
+            "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
+            "ppml_profile", "ppml_kernel_times")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double * 3), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("bc", ctypes.c_int * 6), ("dtype", ctypes.c_int),
+                ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p * 6)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt_next", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("cmax", ctypes.c_double), ("sums", ctypes.c_double * 6),
+                ("steps", ctypes.c_longlong), ("n_vacuum", ctypes.c_longlong),
+                ("n_bad", ctypes.c_longlong), ("flags", ctypes.c_uint)]
+
+
+_vp = ctypes.c_void_p
+_lib.ppml_init_grid.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), _vp, ctypes.POINTER(_vp)]
+_lib.ppml_free_grid.argtypes = [_vp]
+_lib.ppml_cfl_dt.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(ctypes.c_double), _vp]
+_lib.ppml_step.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), ctypes.c_double, _vp]
+_lib.ppml_eulerian_stage.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), ctypes.c_double, _vp]
+_lib.ppml_conserved_sums.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(ctypes.c_double), _vp]
+_lib.ppml_read_diag.argtypes = [_vp, ctypes.POINTER(Diag), _vp]
+_lib.ppml_dt_device.argtypes = [_vp]
+_lib.ppml_dt_device.restype = _vp
+_lib.ppml_batch_init.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.ppml_batch_step.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
+_lib.ppml_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]
+_lib.ppml_batch_free.argtypes = [_vp]
+_lib.ppml_last_error.restype = ctypes.c_char_p
+_lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+
+
+class PPMLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ppml error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != PPML_OK:
+        raise PPMLError(rc, _lib.ppml_last_error().decode())
+
+
+def lib():
+    return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def torch_dtype(dtype: int):
+    return torch.float64 if dtype == PPML_F64 else torch.float32
+
+
+def _state(fields, dtype=None, shape=None) -> State:
+    if len(fields) != 6:
+        raise ValueError("a state has six fields")
+    s = State()
+    for i, t in enumerate(fields):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("state fields must be contiguous CUDA tensors")
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError(f"field {i} has dtype {t.dtype}, expected {dtype}")
+        if shape is not None and t.numel() != shape:
+            raise ValueError(f"field {i} has {t.numel()} elements, expected {shape}")
+        s.f[i] = t.data_ptr()
+    return s
+
+
+class Grid:
+    """Handle over ppml_init_grid / ppml_step / ppml_cfl_dt / ppml_read_diag."""
+
+    def __init__(self, n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, u0=None,
+                 vacuum_frac=1e-5, t_end=0.0, stream=None):
+        d = GridDesc()
+        d.nx, d.ny, d.nz = (int(x) for x in n)
+        for a in range(3):
+            d.h[a] = float(h[a])
+        d.gamma, d.cfl = float(gamma), float(cfl)
+        for q in range(6):
+            d.bc[q] = int(bc[q])
+        d.dtype = int(dtype)
+        d.vacuum_frac = float(vacuum_frac)
+        d.t_end = float(t_end)
+        self.desc = d
+        self.n = tuple(int(x) for x in n)
+        self.cells = self.n[0] * self.n[1] * self.n[2]
+        self.dtype = int(dtype)
+        self.tdtype = torch_dtype(dtype)
+        self._h = ctypes.c_void_p()
+        st = _state(u0, self.tdtype, self.cells)
+        _check(_lib.ppml_init_grid(ctypes.byref(d), ctypes.byref(st), _stream(stream),
+                                   ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            _lib.ppml_free_grid(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cfl_dt(self, u, sync=True, stream=None):
+        st = _state(u, self.tdtype, self.cells)
+        out = ctypes.c_double()
+        _check(_lib.ppml_cfl_dt(self._h, ctypes.byref(st), ctypes.byref(out) if sync else None,
+                                _stream(stream)))
+        return out.value if sync else None
+
+    def step(self, u_in, u_out, dt=0.0, stream=None):
+        a = _state(u_in, self.tdtype, self.cells)
+        b = _state(u_out, self.tdtype, self.cells)
+        _check(_lib.ppml_step(self._h, ctypes.byref(a), ctypes.byref(b), float(dt), _stream(stream)))
+
+    def eulerian_stage(self, u_in, u_star, dt, stream=None):
+        a = _state(u_in, self.tdtype, self.cells)
+        b = _state(u_star, self.tdtype, self.cells)
+        _check(_lib.ppml_eulerian_stage(self._h, ctypes.byref(a), ctypes.byref(b), float(dt),
+                                        _stream(stream)))
+
+    def conserved_sums(self, u, stream=None):
+        st = _state(u, self.tdtype, self.cells)
+        out = (ctypes.c_double * 6)()
+        _check(_lib.ppml_conserved_sums(self._h, ctypes.byref(st), out, _stream(stream)))
+        return list(out)
+
+    def diag(self, stream=None, raise_nonphysical=True) -> dict:
+        d = Diag()
+        rc = _lib.ppml_read_diag(self._h, ctypes.byref(d), _stream(stream))
+        if rc != PPML_OK and (rc != PPML_E_NONPHYSICAL or raise_nonphysical):
+            _check(rc)
+        return {"t": d.t, "dt_next": d.dt_next, "vmax": d.vmax, "cmax": d.cmax,
+                "sums": list(d.sums), "steps": d.steps, "n_vacuum": d.n_vacuum,
+                "n_bad": d.n_bad, "flags": d.flags}
+
+    def dt_device_ptr(self) -> int:
+        return _lib.ppml_dt_device(self._h)
+
+    def profile(self, enable: bool):
+        _check(_lib.ppml_profile(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """(ms_eulerian, ms_lagrangian, ms_finalize) accumulated, and the step count."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_longlong()
+        _check(_lib.ppml_kernel_times(self._h, ms, ctypes.byref(n)))
+        return list(ms), n.value
+
+
+class Batch:
+    """Handle over ppml_batch_init / ppml_batch_step / ppml_batch_status."""
+
+    def __init__(self, ncells, h, t_end, gamma, cfl, dtype=PPML_F32, vacuum_frac=1e-5):
+        n = len(ncells)
+        self.n_inst = n
+        self.dtype = int(dtype)
+        self.tdtype = torch_dtype(dtype)
+        self.total = int(sum(int(x) for x in ncells))
+        nc = (ctypes.c_int * n)(*[int(x) for x in ncells])
+        hh = (ctypes.c_double * n)(*[float(x) for x in h])
+        te = (ctypes.c_double * n)(*[float(x) for x in t_end])
+        self._h = ctypes.c_void_p()
+        _check(_lib.ppml_batch_init(n, nc, hh, te, float(gamma), float(cfl), float(vacuum_frac),
+                                    self.dtype, ctypes.byref(self._h)))
+
+    def step(self, fields, max_steps, sync=False, stream=None):
+        if len(fields) != 4:
+            raise ValueError("a batch state has four fields")
+        ptrs = (ctypes.c_void_p * 4)()
+        for i, t in enumerate(fields):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype != self.tdtype or t.numel() != self.total:
+                raise ValueError(f"batch field {i} has the wrong device, layout, dtype or size")
+            ptrs[i] = t.data_ptr()
+        done = ctypes.c_int(-1)
+        _check(_lib.ppml_batch_step(self._h, ptrs, int(max_steps), ctypes.byref(done) if sync else None,
+                                    _stream(stream)))
+        return done.value if sync else None
+
+    def status(self, stream=None):
+        t = (ctypes.c_double * self.n_inst)()
+        s = (ctypes.c_int * self.n_inst)()
+        _check(_lib.ppml_batch_status(self._h, t, s, _stream(stream)))
+        return list(t), list(s)
+
+    def close(self):
+        if self._h:
+            _lib.ppml_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_device(u, dtype: int, device="cuda"):
+    """Six (or four) float64 numpy arrays -> contiguous CUDA tensors of the path's dtype."""
+    return [torch.as_tensor(a).to(device=device, dtype=torch_dtype(dtype)).contiguous().reshape(-1)
+            for a in u]

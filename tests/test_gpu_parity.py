@@ -1,0 +1,364 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L1 per field, sum|gpu - oracle| / sum|oracle|):
+* FP64 path: 1e-10 on every field (rounding order and FMA contraction only);
+* FP32 path: 1e-5 on rho and p for a single step on smooth data, 1e-4 for a shock-tube
+  run (config 1/2/4), 1e-3 for the point blast (config 3).  FP32 conservation sums are
+  FP64 sums of the FP32 state and must stay within 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_01105_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU, skipped there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1607_01105_gb300 import ppml  # noqa: E402
+
+F64, F32 = ppml.PPML_F64, ppml.PPML_F32
+TOL64 = 1e-10
+
+
+def rel_l1(got, ref, scale_ref=None):
+    den = np.abs(ref).sum()
+    if scale_ref is not None:
+        den = max(den, 1e-3 * np.abs(scale_ref).sum())
+    if den == 0.0:
+        return float(np.abs(got).sum())
+    return float(np.abs(got - ref).sum() / den)
+
+
+def host(u, shape):
+    return [t.double().cpu().numpy().reshape(shape) for t in u]
+
+
+def oracle_grid(pb, **kw):
+    return oracle.Grid(pb.n, pb.h, pb.gamma, pb.bc, pb.cfl,
+                       rho_mean=oracle.mean_density(pb.u), **kw)
+
+
+def gpu_grid(pb, dtype, u, **kw):
+    return ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u, **kw)
+
+
+def compare(got, ref, tol, fields=range(6), gamma=None):
+    errs = {}
+    for f in fields:
+        errs[f] = rel_l1(got[f], ref[f], scale_ref=ref[0] if f in (1, 2, 3) else None)
+    bad = {f: e for f, e in errs.items() if not e <= tol}
+    assert not bad, f"relative L1 above {tol}: {bad}"
+    return errs
+
+
+def shape_of(pb):
+    return (pb.n[2], pb.n[1], pb.n[0])
+
+
+# ----------------------------------------------------------------------- stage level
+
+@pytest.mark.parametrize("bc", [(0,) * 6, (1,) * 6, (2,) * 6, (2, 0, 1, 1, 0, 2)])
+def test_eulerian_stage_fp64(bc):
+    pb = inputs.random_rough(n=(19, 13, 11), bc=bc)
+    g = oracle_grid(pb)
+    dt = 0.5 * oracle.cfl_dt(g, pb.u)
+    _, _, ustar = oracle.step(g, pb.u, dt, want_star=True)
+    u = ppml.to_device(pb.u, F64)
+    out = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.eulerian_stage(u, out, dt)
+    compare(host(out, shape_of(pb)), ustar, TOL64)
+
+
+# ------------------------------------------------------------------------ full step
+
+CASES = {
+    "rough_outflow_3d": lambda: inputs.random_rough(n=(19, 13, 11)),
+    "rough_periodic_3d": lambda: inputs.random_rough(n=(17, 12, 9), bc=(1,) * 6),
+    "rough_reflect_3d": lambda: inputs.random_rough(n=(16, 11, 10), bc=(2,) * 6),
+    "smooth_mixed_3d": lambda: inputs.random_smooth(n=(21, 14, 10), bc=(2, 0, 1, 1, 0, 2)),
+    "rough_2d": lambda: inputs.random_rough(n=(37, 29, 1), bc=(0, 0, 1, 1, 0, 0)),
+    "rough_1d": lambda: inputs.random_rough(n=(301, 1, 1), bc=(0, 0, 0, 0, 0, 0)),
+    "min_cells_3d": lambda: inputs.random_rough(n=(3, 3, 3), bc=(1,) * 6),
+    "point_blast_16": lambda: inputs.point_blast_3d(n=16),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_step_fp64_matches_oracle(case):
+    """Three steps with the device-resident CFL step (dt <= 0 path) against the oracle."""
+    pb = CASES[case]()
+    g = oracle_grid(pb)
+    shape = shape_of(pb)
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    ref = pb.u
+    for s in range(3):
+        dt = oracle.cfl_dt(g, ref)
+        ref, dg = oracle.step(g, ref, dt)
+        grid.step(u, v, 0.0)
+        u, v = v, u
+    d = grid.diag()
+    got = host(u, shape)
+    compare(got, ref, TOL64)
+    assert d["dt_next"] == pytest.approx(dg["dt_cfl"], rel=1e-10)
+    for f in range(6):
+        assert d["sums"][f] == pytest.approx(dg["sums"][f], rel=1e-10,
+                                             abs=1e-10 * abs(dg["sums"][0]))
+    assert d["steps"] == 3 and d["n_bad"] == 0
+
+
+@pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_2d", "point_blast_16"])
+def test_step_fp32_single_step(case):
+    """One FP32 step from the same (FP32-representable) input as the oracle."""
+    pb = CASES[case]()
+    pb.u = [a.astype(np.float32).astype(np.float64) for a in pb.u]
+    g = oracle_grid(pb)
+    dt = oracle.cfl_dt(g, pb.u)
+    ref, dg = oracle.step(g, pb.u, dt)
+    u = ppml.to_device(pb.u, F32)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F32, u)
+    grid.step(u, v, dt)
+    got = host(v, shape_of(pb))
+    tol = 1e-4 if case == "point_blast_16" else 1e-5
+    compare(got, ref, tol, fields=(0, 5))
+
+
+def test_explicit_dt_and_ragged_blocks():
+    """Host dt path on a grid whose cell count is not a multiple of the block size."""
+    pb = inputs.random_smooth(n=(23, 7, 5), bc=(1,) * 6)
+    g = oracle_grid(pb)
+    dt = 0.37 * oracle.cfl_dt(g, pb.u)
+    ref, _ = oracle.step(g, pb.u, dt)
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.step(u, v, dt)
+    compare(host(v, shape_of(pb)), ref, TOL64)
+    assert grid.diag()["t"] == pytest.approx(dt, rel=1e-15)
+
+
+def test_uniform_flow_and_zero_dt():
+    pb = inputs.uniform_flow()
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.step(u, v, 0.0)
+    for a, b in zip(host(v, shape_of(pb)), pb.u):
+        assert np.max(np.abs(a - b)) <= 1e-14 * max(1.0, np.max(np.abs(b)))
+    # dt = 0 through a finished run: t_end reached, device step is 0, state unchanged
+    g2 = gpu_grid(pb, F64, u, t_end=1e-12)
+    g2.step(u, v, 0.0)
+    d = g2.diag()
+    assert d["t"] == pytest.approx(1e-12) and d["dt_next"] == 0.0
+    assert d["flags"] & ppml.FLAG_DT_ZERO
+
+
+def test_cfl_dt_and_sums_match_oracle():
+    pb = inputs.random_rough(n=(30, 20, 10))
+    g = oracle_grid(pb)
+    dgo = oracle.diagnostics(g, pb.u)
+    for dtype, tol in ((F64, 1e-13), (F32, 1e-6)):
+        u = ppml.to_device(pb.u, dtype)
+        grid = gpu_grid(pb, dtype, u)
+        assert grid.cfl_dt(u) == pytest.approx(dgo["dt_cfl"], rel=tol)
+        sums = grid.conserved_sums(u)
+        for f in range(6):
+            assert sums[f] == pytest.approx(dgo["sums"][f], rel=tol, abs=tol * abs(dgo["sums"][0]))
+
+
+def test_nonphysical_flagged():
+    pb = inputs.random_smooth(n=(8, 8, 8))
+    pb.u[0][2, 3, 4] = -1.0  # negative density planted in the host input
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.step(u, v, 1e-4)
+    with pytest.raises(ppml.PPMLError) as e:
+        grid.diag()
+    assert e.value.code == ppml.PPML_E_NONPHYSICAL
+    d = grid.diag(raise_nonphysical=False)
+    assert d["flags"] & ppml.FLAG_NONPHYSICAL and d["n_bad"] > 0
+
+
+# ------------------------------------------------------------------ configurations
+
+def run_gpu(pb, dtype, t_end=None, max_steps=100000):
+    """Advance on the GPU with the device-resident CFL step, clipped at t_end."""
+    u = ppml.to_device(pb.u, dtype)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, dtype, u, t_end=t_end or pb.t_end)
+    steps = 0
+    d = grid.diag()
+    while d["dt_next"] > 0.0 and steps < max_steps:
+        grid.step(u, v, 0.0)
+        u, v = v, u
+        steps += 1
+        d = grid.diag()
+    return host(u, shape_of(pb)), d, steps
+
+
+def test_config1_sod_fp64_and_fp32():
+    """1D Sod, 256 cells, gamma 1.4, CFL 0.4, outflow, t = 0.2."""
+    pb = inputs.sod_1d(256)
+    g = oracle_grid(pb)
+    ref, t, steps_o, dgo = oracle.run(g, pb.u, pb.t_end)
+    got, d, steps = run_gpu(pb, F64)
+    assert steps == steps_o and d["t"] == pytest.approx(0.2, rel=1e-14)
+    compare(got, ref, TOL64)
+    got32, d32, steps32 = run_gpu(pb, F32)
+    assert d32["t"] == pytest.approx(0.2, rel=1e-12)
+    e = compare(got32, ref, 1e-4, fields=(0, 5))
+    for f in (0, 4):  # mass and total energy: conserved
+        assert d32["sums"][f] == pytest.approx(dgo["sums"][f], rel=1e-6)
+
+
+def test_config2_planar_128_fp64_fp32():
+    """3D planar shock tube 128^3 (outflow x, periodic y z): parity over 3 steps, and the
+    GPU output stays exactly uniform in y and z."""
+    pb = inputs.planar_sod_3d(128)
+    g = oracle_grid(pb)
+    ref = pb.u
+    dts = []
+    for _ in range(3):
+        dts.append(oracle.cfl_dt(g, ref))
+        ref, dgo = oracle.step(g, ref, dts[-1])
+    for dtype, tol in ((F64, TOL64), (F32, 1e-5)):
+        u = ppml.to_device(pb.u, dtype)
+        v = [torch.empty_like(x) for x in u]
+        grid = gpu_grid(pb, dtype, u)
+        for dt in dts:
+            grid.step(u, v, dt)
+            u, v = v, u
+        got = host(u, shape_of(pb))
+        compare(got, ref, tol, fields=(0, 1, 4, 5))
+        for f in range(6):
+            assert np.all(got[f] == got[f][:1, :1, :])
+
+
+def test_config3_point_blast_256_fp32():
+    """3D point blast 256^3 (the timed workload) in FP32: two steps against the FP64
+    oracle, mirror symmetry of the GPU output, FP64 sums."""
+    pb = inputs.point_blast_3d(256)
+    g = oracle_grid(pb)
+    ref = pb.u
+    dts = []
+    for _ in range(2):
+        dts.append(oracle.cfl_dt(g, ref))
+        ref, dgo = oracle.step(g, ref, dts[-1])
+    u = ppml.to_device(pb.u, F32)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F32, u)
+    for dt in dts:
+        grid.step(u, v, dt)
+        u, v = v, u
+    got = host(u, shape_of(pb))
+    compare(got, ref, 1e-3, fields=(0, 5))
+    rho = got[0]
+    assert np.max(np.abs(rho - rho[:, :, ::-1])) <= 1e-5 * np.max(rho)
+    d = grid.diag()
+    assert d["sums"][0] == pytest.approx(dgo["sums"][0], rel=1e-6)
+    assert d["sums"][4] == pytest.approx(dgo["sums"][4], rel=1e-6)
+
+
+def test_config3_point_blast_64_fp64_run():
+    """Point blast at 64^3 in FP64 for 40 steps against the oracle (1e-10)."""
+    pb = inputs.point_blast_3d(64)
+    g = oracle_grid(pb)
+    ref = pb.u
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    for _ in range(40):
+        ref, dgo = oracle.step(g, ref, oracle.cfl_dt(g, ref))
+        grid.step(u, v, 0.0)
+        u, v = v, u
+    compare(host(u, shape_of(pb)), ref, TOL64)
+
+
+# ---------------------------------------------------------------- batched 1D (cfg 4)
+
+_BATCH_CACHE = {}
+
+
+def _batch_oracle(b, i):
+    key = (int(b.offsets[-1]), i)
+    if key not in _BATCH_CACHE:
+        _BATCH_CACHE[key] = _batch_oracle_run(b, i)
+    return _BATCH_CACHE[key]
+
+
+def _batch_oracle_run(b, i):
+    n = int(b.ncells[i])
+    sl = slice(b.offsets[i], b.offsets[i + 1])
+    z = np.zeros(n)
+    u = [b.u[0][sl], b.u[1][sl], z, z, b.u[2][sl], b.u[3][sl]]
+    g = oracle.Grid((n, 1, 1), (float(b.h[i]), 1.0, 1.0), b.gamma, (0,) * 6, b.cfl,
+                    rho_mean=float(np.mean(b.u[0][sl])))
+    ref, t, steps, dg = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]))
+    return ref, steps
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_config4_batch_matches_oracle(dtype):
+    """Batched uneven Riemann problems: a 24-instance batch, every instance against its
+    own 1D oracle run (FP64: 1e-10; FP32: 1e-4 on rho and p)."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=24, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, dtype)
+    st = [torch.as_tensor(a).to("cuda", ppml.torch_dtype(dtype)) for a in b.u]
+    done = 0
+    for _ in range(100):
+        done = bt.step(st, 1000, sync=True)
+        if done == b.ncells.size:
+            break
+    assert done == b.ncells.size
+    t, steps = bt.status()
+    assert np.allclose(t, b.t_end, rtol=1e-14)
+    got = [x.double().cpu().numpy() for x in st]
+    tol = TOL64 if dtype == F64 else 1e-4
+    for i in range(b.ncells.size):
+        ref, steps_o = _batch_oracle(b, i)
+        assert abs(steps[i] - steps_o) <= (0 if dtype == F64 else 1)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        flds = ((0, 0), (1, 1), (2, 4), (3, 5)) if dtype == F64 else ((0, 0), (3, 5))
+        for k, f in flds:
+            e = rel_l1(got[k][sl], ref[f].ravel(), scale_ref=ref[0].ravel() if f == 1 else None)
+            assert e <= tol, (i, f, e)
+
+
+def test_cuda_graph_replay_equals_eager():
+    """Steps using the device-resident dt can be captured in a CUDA graph; replaying the
+    graph gives bitwise the eager result."""
+    pb = inputs.random_smooth(n=(32, 24, 16), bc=(1,) * 6)
+    a = ppml.to_device(pb.u, F32)
+    b = [torch.empty_like(x) for x in a]
+    ge = gpu_grid(pb, F32, a)
+    ea, eb = [x.clone() for x in a], [torch.empty_like(x) for x in a]
+    for _ in range(2):
+        ge.step(ea, eb, 0.0)
+        ge.step(eb, ea, 0.0)
+    torch.cuda.synchronize()
+    gg = gpu_grid(pb, F32, a)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            gg.step(a, b, 0.0, stream=s)
+            gg.step(b, a, 0.0, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(a, ea):
+        assert torch.equal(x, y)
+    assert gg.diag()["steps"] == 4
