@@ -1,0 +1,240 @@
+// Batched independent 1D problems (many shock tubes of uneven lengths) advanced by one
+// persistent launch: each CTA owns one instance, keeps its four fields (rho, m, rho E,
+// rho eps) resident in shared memory for all of its steps, takes its own CFL step from a
+// CTA-local reduction (Sec. 1.1) and stops at its own end time.  The scheme per step is
+// the 1D case of Sec. 1: Eulerian face solve, upwind Lagrangian fluxes, energy
+// correction of Sec. 1.4.  In 1D the 9-point template (eq. veltemplate) runs on the cell
+// itself (its transverse neighbours are the cell), evaluated term by term.  Outflow
+// boundaries on both ends.  CTAs never wait on one another.
+#pragma once
+#include "ppml_device.cuh"
+
+namespace ppml {
+
+constexpr int kBatchThreads = 512;
+constexpr int kBatchGhost = 3;
+
+struct InstDev {
+  long long off;  // first cell in the packed arrays
+  int n;          // cells
+  int steps;      // steps taken so far
+  double h, t_end, t, rho_vac;
+  int done, pad;
+};
+
+// Parabolas of the cells left and right of a face from the six values q[0..5] around it
+// (face between q[2] and q[3]): Appendix Steps 1-3.
+template <typename T>
+__device__ __forceinline__ void pair_parabolas(const T q[6], Parab<T>& PL, Parab<T>& PR) {
+  T d[4];
+#pragma unroll
+  for (int k = 1; k <= 4; k++) d[k - 1] = limited_slope(q[k - 1], q[k], q[k + 1]);
+  const T f12 = face_value(q[1], q[2], d[0], d[1]);
+  const T f23 = face_value(q[2], q[3], d[1], d[2]);
+  const T f34 = face_value(q[3], q[4], d[2], d[3]);
+  PL = parabola(q[2], f12, f23);
+  PR = parabola(q[3], f23, f34);
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_ghosts_1d(T* q, int n) {
+  const int t = threadIdx.x;
+  if (t < kBatchGhost)
+    q[t] = q[kBatchGhost];
+  else if (t < 2 * kBatchGhost)
+    q[n + kBatchGhost + (t - kBatchGhost)] = q[n + kBatchGhost - 1];
+}
+
+// eq. veltemplate on a cell whose transverse neighbours are itself
+template <typename T>
+__device__ __forceinline__ T template_1d(T v) {
+  const T four = v + v + v + v;
+  return four / T(16) + four / T(8) + v / T(4);
+}
+
+__device__ __forceinline__ double block_max_sum(double a, double b, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[w] = a;
+    sh[32 + w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0.0, B = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+      A = fmax(A, sh[q]);
+      B = fmax(B, sh[32 + q]);
+    }
+    sh[64] = A + B;
+  }
+  __syncthreads();
+  const double r = sh[64];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(T* __restrict__ g_rho,
+                                                              T* __restrict__ g_m,
+                                                              T* __restrict__ g_en,
+                                                              T* __restrict__ g_ei,
+                                                              InstDev* __restrict__ inst,
+                                                              const int* __restrict__ order,
+                                                              double gamma_d, double cfl,
+                                                              int max_steps, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[80];
+  const int id = order[blockIdx.x];
+  InstDev I = inst[id];
+  if (I.done) return;
+  const int n = I.n;
+  const int stride = nmax + 2 * kBatchGhost;
+  T* R = (T*)smem_raw;
+  T* M = R + stride;
+  T* E = M + stride;
+  T* Ei = E + stride;
+  T* FA = Ei + stride;      // face array A (V, then v hat)
+  T* FB = FA + (nmax + 1);  // face array B (P, then fluxes)
+  const int tid = threadIdx.x;
+  for (int c = tid; c < n; c += blockDim.x) {
+    R[c + kBatchGhost] = g_rho[I.off + c];
+    M[c + kBatchGhost] = g_m[I.off + c];
+    E[c + kBatchGhost] = g_en[I.off + c];
+    Ei[c + kBatchGhost] = g_ei[I.off + c];
+  }
+  __syncthreads();
+  const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
+  if (I.steps == 0 && I.rho_vac < 0.0) {
+    // vacuum threshold reference: the instance's mean initial density
+    double s = 0.0;
+    for (int c = tid; c < n; c += blockDim.x) s += (double)R[c + kBatchGhost];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double S = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); q++) S += red[q];
+      red[79] = S / n;
+    }
+    __syncthreads();
+    I.rho_vac = -I.rho_vac * red[79];  // stored as the negated fraction before the first call
+    __syncthreads();
+  }
+  for (int s = 0; s < max_steps; s++) {
+    // CFL step of the current state (Sec. 1.1), per cell in the checker's order
+    double vm = 0.0, cm = 0.0;
+    for (int c = tid; c < n; c += blockDim.x) {
+      const T r = R[c + kBatchGhost];
+      const T vx = M[c + kBatchGhost] / r, vy = T(0) / r, vz = T(0) / r;
+      const T v = sqrt(vx * vx + vy * vy + vz * vz);
+      const T p = gm1 * Ei[c + kBatchGhost];
+      const T cs = sqrt(gamma * p / r);
+      vm = fmax(vm, (double)v);
+      cm = fmax(cm, (double)cs);
+    }
+    const double den = block_max_sum(vm, cm, red);
+    double dt = cfl * I.h / den;
+    if (dt > I.t_end - I.t) dt = I.t_end - I.t;
+    if (!(dt > 0.0)) {
+      I.done = 1;
+      break;
+    }
+    const T th = T(dt / I.h);
+    fill_ghosts_1d(R, n);
+    fill_ghosts_1d(M, n);
+    fill_ghosts_1d(E, n);
+    fill_ghosts_1d(Ei, n);
+    __syncthreads();
+    // Eulerian stage: faces f = 0..n between padded cells f+2 and f+3
+    for (int f = tid; f <= n; f += blockDim.x) {
+      T v[6], p[6];
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        v[q] = M[f + q] / R[f + q];
+        p[q] = gm1 * Ei[f + q];
+      }
+      Parab<T> vL, vR, pL, pR;
+      pair_parabolas(v, vL, vR);
+      pair_parabolas(p, pL, pR);
+      T lam, Z;
+      face_constants(R[f + 2], R[f + 3], p[2], p[3], gamma, lam, Z);
+      const T y = Prec<T>::courant(lam, dt, I.h, th);
+      T V, P;
+      riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
+                 avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
+      FA[f] = V;
+      FB[f] = P;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) {
+      const int g = c + kBatchGhost;
+      const T Vm = FA[c], Vp = FA[c + 1], Pm = FB[c], Pp = FB[c + 1];
+      const T ei0 = Ei[g];
+      M[g] = M[g] - th * (Pp - Pm);
+      E[g] = E[g] - th * (Pp * Vp - Pm * Vm);
+      Ei[g] = ei0 - gm1 * ei0 * (th * (Vp - Vm));
+    }
+    __syncthreads();
+    fill_ghosts_1d(M, n);
+    fill_ghosts_1d(E, n);
+    fill_ghosts_1d(Ei, n);
+    __syncthreads();
+    // Lagrangian stage: v hat at faces, then each field's flux and update
+    for (int f = tid; f <= n; f += blockDim.x) {
+      const T rl = R[f + 2], rr = R[f + 3];
+      const T sl = sqrt(rl), sr = sqrt(rr);
+      const T vtl = template_1d(M[f + 2] / rl), vtr = template_1d(M[f + 3] / rr);
+      FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
+    }
+    __syncthreads();
+    T* fields[4] = {R, M, E, Ei};
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+      T* q = fields[k];
+      for (int f = tid; f <= n; f += blockDim.x) {
+        T w[6];
+#pragma unroll
+        for (int o = 0; o < 6; o++) w[o] = q[f + o];
+        Parab<T> PL, PR;
+        pair_parabolas(w, PL, PR);
+        const T vh = FA[f];
+        const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
+        FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y) : vh * avg_left(PR.L, PR.D, PR.S, y);
+      }
+      __syncthreads();
+      for (int c = tid; c < n; c += blockDim.x)
+        q[c + kBatchGhost] = q[c + kBatchGhost] - th * (FB[c + 1] - FB[c]);
+      __syncthreads();
+    }
+    // Sec. 1.4 energy consistency
+    for (int c = tid; c < n; c += blockDim.x) {
+      const int g = c + kBatchGhost;
+      T u[6] = {R[g], M[g], T(0), T(0), E[g], Ei[g]};
+      correct_energy<T>(u, I.rho_vac);
+      M[g] = u[1];
+      Ei[g] = u[5];
+    }
+    __syncthreads();
+    I.t = (I.t + dt > I.t_end) ? I.t_end : I.t + dt;
+    I.steps += 1;
+    if (I.t >= I.t_end) {
+      I.done = 1;
+      break;
+    }
+  }
+  for (int c = tid; c < n; c += blockDim.x) {
+    g_rho[I.off + c] = R[c + kBatchGhost];
+    g_m[I.off + c] = M[c + kBatchGhost];
+    g_en[I.off + c] = E[c + kBatchGhost];
+    g_ei[I.off + c] = Ei[c + kBatchGhost];
+  }
+  if (tid == 0) inst[id] = I;
+}
+
+}  // namespace ppml

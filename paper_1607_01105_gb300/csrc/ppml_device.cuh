@@ -7,11 +7,40 @@
 //   * rho_L, rho_R, p_L, p_R inside the Roe averages, lambda and the impedance are the
 //     adjacent cell values; only v and p carrying (-+ lambda t) are parabola averages;
 //   * the monotonicity step tests "flat" first, then applies at most one overshoot fix.
+//
+// Precision policy.  The double instantiation is compiled without FMA contraction and
+// evaluates every expression in the same order as the FP64 checker (x/6, 2y/3,
+// (speed * tau) / h), so the FP64 path reproduces it bit for bit.  The float
+// instantiation uses the cheaper forms (x * (1/6), y * (2/3), speed * (tau/h)) and FMAs.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace ppml {
+
+template <typename T>
+struct Prec;
+
+template <>
+struct Prec<float> {
+  static __device__ __forceinline__ float div6(float x) { return x * (1.0f / 6.0f); }
+  static __device__ __forceinline__ float two_thirds(float y) { return y * (2.0f / 3.0f); }
+  // Courant number of a signal speed s: s * tau / h with th = tau / h precomputed.
+  static __device__ __forceinline__ float courant(float s, double /*tau*/, double /*h*/,
+                                                  float th) {
+    return s * th;
+  }
+};
+
+template <>
+struct Prec<double> {
+  static __device__ __forceinline__ double div6(double x) { return x / 6.0; }
+  static __device__ __forceinline__ double two_thirds(double y) { return 2.0 * y / 3.0; }
+  static __device__ __forceinline__ double courant(double s, double tau, double h,
+                                                   double /*th*/) {
+    return s * tau / h;
+  }
+};
 
 template <typename T>
 struct Parab {
@@ -36,7 +65,7 @@ __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
 // Appendix, Step 1: 4th-order face value q_{i+1/2} from the cell values and limited slopes.
 template <typename T>
 __device__ __forceinline__ T face_value(T q0, T q1, T d0, T d1) {
-  return T(0.5) * (q0 + q1) - (d1 - d0) * T(1.0 / 6.0);
+  return T(0.5) * (q0 + q1) - Prec<T>::div6(d1 - d0);
 }
 
 // Appendix, Steps 2-3: parabola of a cell from its value and its two face values.
@@ -64,53 +93,32 @@ __device__ __forceinline__ Parab<T> parabola(T q0, T L, T R) {
 // Appendix, characteristic integrals: mean of the parabola over the right fraction y of
 // the cell (q_L(-lambda t), y = lambda t / h) ...
 template <typename T>
-__device__ __forceinline__ T avg_right(const Parab<T>& p, T y) {
-  return p.R - T(0.5) * y * (p.D - p.S * (T(1) - y * T(2.0 / 3.0)));
+__device__ __forceinline__ T avg_right(T R, T D, T S, T y) {
+  return R - T(0.5) * y * (D - S * (T(1) - Prec<T>::two_thirds(y)));
 }
 // ... and over its left fraction y (q_R(lambda t)).
 template <typename T>
-__device__ __forceinline__ T avg_left(const Parab<T>& p, T y) {
-  return p.L + T(0.5) * y * (p.D + p.S * (T(1) - y * T(2.0 / 3.0)));
+__device__ __forceinline__ T avg_left(T L, T D, T S, T y) {
+  return L + T(0.5) * y * (D + S * (T(1) - Prec<T>::two_thirds(y)));
 }
 
-// Parabolas of the three middle cells (offsets -1, 0, +1) of a 7-cell window q[0..6].
+// Sec. 1.1/1.2: face constants of the acoustic Riemann problem from the adjacent cell
+// values: lambda = sqrt(gamma p^/rho^) and the impedance Z = rho^ lambda.
 template <typename T>
-__device__ __forceinline__ void window_parabolas(const T q[7], Parab<T> P[3]) {
-  T d[5];
-#pragma unroll
-  for (int k = 1; k <= 5; k++) d[k - 1] = limited_slope(q[k - 1], q[k], q[k + 1]);
-  T f[4];  // faces between window cells k and k+1, k = 1..4
-#pragma unroll
-  for (int k = 1; k <= 4; k++) f[k - 1] = face_value(q[k], q[k + 1], d[k - 1], d[k]);
-#pragma unroll
-  for (int c = 0; c < 3; c++) P[c] = parabola(q[c + 2], f[c], f[c + 1]);
-}
-
-// Sec. 1.1/1.2: acoustic Riemann solution at a face.  rl, rr, pl, pr: adjacent cell values;
-// the parabolas of v and p of the left and right cells; tau_h = tau / h.
-template <typename T>
-__device__ __forceinline__ void face_riemann(T rl, T rr, T pl, T pr, const Parab<T>& vL,
-                                             const Parab<T>& vR, const Parab<T>& pL,
-                                             const Parab<T>& pR, T gamma, T tau_h, T& V, T& P) {
+__device__ __forceinline__ void face_constants(T rl, T rr, T pl, T pr, T gamma, T& lam, T& Z) {
   const T sl = sqrt(rl), sr = sqrt(rr);
   const T A = rl * sl + rr * sr;  // rho_L^{3/2} + rho_R^{3/2}
   const T B = pl * sl + pr * sr;  // p_L sqrt(rho_L) + p_R sqrt(rho_R)
   const T S = sl + sr;
-  const T lam = sqrt(gamma * B / A);  // lambda = sqrt(gamma p^/rho^)
-  const T y = lam * tau_h;
-  const T vls = avg_right(vL, y), vrs = avg_left(vR, y);
-  const T pls = avg_right(pL, y), prs = avg_left(pR, y);
-  const T Z = sqrt(gamma * A * B / (S * S));  // impedance rho^ lambda
-  V = T(0.5) * (vls + vrs) + (pls - prs) / (T(2) * Z);
-  P = T(0.5) * (pls + prs) + T(0.5) * Z * (vls - vrs);
+  lam = sqrt(gamma * B / A);
+  Z = sqrt(gamma * A * B / (S * S));
 }
 
-// Sec. 1.3, eq. fluxonlagrangestage: upwind flux through a face with velocity vh between
-// the cells with parabolas PL and PR.
+// eqs. lowriemannvelocity / lowriemannpressure from the four characteristic averages.
 template <typename T>
-__device__ __forceinline__ T upwind_flux(T vh, const Parab<T>& PL, const Parab<T>& PR, T tau_h) {
-  const T y = tabs(vh) * tau_h;
-  return vh >= T(0) ? vh * avg_right(PL, y) : vh * avg_left(PR, y);
+__device__ __forceinline__ void riemann_vp(T vls, T vrs, T pls, T prs, T Z, T& V, T& P) {
+  V = T(0.5) * (vls + vrs) + (pls - prs) / (T(2) * Z);
+  P = T(0.5) * (pls + prs) + T(0.5) * Z * (vls - vrs);
 }
 
 // Sec. 1.4: energy consistency of one cell, in double.  u = {rho, mx, my, mz, rhoE, rhoeps}.
@@ -138,6 +146,78 @@ __device__ __forceinline__ int energy_correction(double u[6], double rho_vac) {
   return 0;
 }
 
+// ---------------------------------------------------------- compensated FP32 helpers
+// Error-free transformations (Knuth TwoSum; FMA-based TwoProduct).  Used where the
+// paper's quantity is a small difference of large totals so that the FP32 path keeps
+// FP64-class accuracy without GB300's reduced-rate FP64 pipe.
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// rho eps = rho E - |m|^2 / (2 rho) evaluated in double-float (about 44 significant
+// bits) and rounded once to float.  Sec. 1.4 (dense branch).
+__device__ __forceinline__ float internal_energy_ff(float rho, float mx, float my, float mz,
+                                                    float en) {
+  const float p1 = mx * mx, e1 = fmaf(mx, mx, -p1);
+  const float p2 = my * my, e2 = fmaf(my, my, -p2);
+  const float p3 = mz * mz, e3 = fmaf(mz, mz, -p3);
+  float s, t1, hi, t2;
+  two_sum(p1, p2, s, t1);
+  two_sum(s, p3, hi, t2);
+  const float lo = ((t1 + t2) + (e1 + e2)) + e3;  // |m|^2 = hi + lo
+  const float r2 = 2.0f * rho;
+  const float q = hi / r2;
+  const float rem = fmaf(-q, r2, hi) + lo;  // exact remainder of hi plus lo
+  const float ql = rem / r2;                // |m|^2/(2 rho) = q + ql
+  float d, de;
+  two_sum(en, -q, d, de);
+  return d + (de - ql);
+}
+
+// Neumaier-compensated running sum in float; value() = hi + lo in double.
+struct CompSum {
+  float hi, lo;
+  __device__ __forceinline__ void init() { hi = 0.f; lo = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x;
+    if (fabsf(hi) >= fabsf(x))
+      lo += (hi - t) + x;
+    else
+      lo += (x - t) + hi;
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Sec. 1.4 energy correction in the state's precision class: double computes it in
+// double; float computes the dense branch in double-float and the (rare) vacuum branch
+// in double.  Returns 1 for the vacuum branch.
+template <typename T>
+__device__ __forceinline__ int correct_energy(T u[6], double rho_vac);
+template <>
+__device__ __forceinline__ int correct_energy<double>(double u[6], double rho_vac) {
+  return energy_correction(u, rho_vac);
+}
+template <>
+__device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac) {
+  const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  if ((double)u[0] < rho_vac && m2 > 0.f) {
+    double d[6] = {u[0], u[1], u[2], u[3], u[4], u[5]};
+    energy_correction(d, rho_vac);
+    u[1] = (float)d[1];
+    u[2] = (float)d[2];
+    u[3] = (float)d[3];
+    u[5] = (float)d[5];
+    return 1;
+  }
+  const float e = internal_energy_ff(u[0], u[1], u[2], u[3], u[4]);
+  if (e > 0.f) u[5] = e;
+  return 0;
+}
+
 // Boundary handling by index mapping: interior coordinate read for coordinate c of an
 // axis with n cells (outflow: clamp; periodic: wrap; reflecting: mirror, flip = 1).
 __device__ __forceinline__ int bc_map(int c, int n, int lo, int hi, int& flip) {
@@ -162,17 +242,23 @@ struct GridGeom {
   long long nxy, ncell;
 };
 
-// Value of field `f` (0..5) at possibly out-of-domain cell (i, j, k), with the momentum
-// component normal to a reflecting wall negated.
+// Linear index of possibly out-of-domain cell (i, j, k) after boundary mapping; fl[a] is
+// set when axis a was mirrored (the a-momentum changes sign there).
+__device__ __forceinline__ long long map_cell(int i, int j, int k, const GridGeom& g, int fl[3]) {
+  const int ii = bc_map(i, g.n[0], g.bc[0], g.bc[1], fl[0]);
+  const int jj = bc_map(j, g.n[1], g.bc[2], g.bc[3], fl[1]);
+  const int kk = bc_map(k, g.n[2], g.bc[4], g.bc[5], fl[2]);
+  return (long long)ii + (long long)g.n[0] * jj + g.nxy * kk;
+}
+
+// Value of field `f` (0..5; -1 for a scalar without sign flips) at possibly out-of-domain
+// cell (i, j, k), with the momentum component normal to a reflecting wall negated.
 template <typename T>
 __device__ __forceinline__ T load_bc(const T* __restrict__ q, int f, int i, int j, int k,
                                      const GridGeom& g) {
-  int fx, fy, fz;
-  const int ii = bc_map(i, g.n[0], g.bc[0], g.bc[1], fx);
-  const int jj = bc_map(j, g.n[1], g.bc[2], g.bc[3], fy);
-  const int kk = bc_map(k, g.n[2], g.bc[4], g.bc[5], fz);
-  T v = __ldg(q + (long long)ii + (long long)g.n[0] * jj + g.nxy * kk);
-  if ((f == 1 && fx) || (f == 2 && fy) || (f == 3 && fz)) v = -v;
+  int fl[3];
+  T v = __ldg(q + map_cell(i, j, k, g, fl));
+  if ((f == 1 && fl[0]) || (f == 2 && fl[1]) || (f == 3 && fl[2])) v = -v;
   return v;
 }
 

@@ -1,0 +1,43 @@
+// Host-side launchers of the stencil kernels, instantiated once per precision in
+// ppml_kern_f32.cu (FMA contraction on) and ppml_kern_f64.cu (contraction off, so the
+// FP64 path evaluates every expression exactly as written).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "ppml_batch.cuh"
+#include "ppml_march.cuh"
+
+namespace ppml {
+
+template <typename T>
+int prepare_kernels();  // opt-in shared-memory sizes; call outside stream capture
+template <typename T>
+int launch_eulerian(const MarchArgs<T>& A, int nblk, cudaStream_t st);
+template <typename T>
+int launch_lagrangian(const MarchArgs<T>& A, int nblk, cudaStream_t st);
+template <typename T>
+int launch_diag(const MarchArgs<T>& A, int nblk, cudaStream_t st);
+template <typename T>
+int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
+                 double cfl, int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st);
+
+// explicit specializations live in ppml_kern_f32.cu / ppml_kern_f64.cu
+#define PPML_DECLARE_LAUNCHERS(R)                                                            \
+  template <>                                                                                \
+  int prepare_kernels<R>();                                                                  \
+  template <>                                                                                \
+  int launch_eulerian<R>(const MarchArgs<R>& A, int nblk, cudaStream_t st);                   \
+  template <>                                                                                \
+  int launch_lagrangian<R>(const MarchArgs<R>& A, int nblk, cudaStream_t st);                 \
+  template <>                                                                                \
+  int launch_diag<R>(const MarchArgs<R>& A, int nblk, cudaStream_t st);                       \
+  template <>                                                                                \
+  int launch_batch<R>(R * rho, R * m, R * en, R * ei, InstDev * inst, const int* order,       \
+                      double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem, \
+                      cudaStream_t st);
+PPML_DECLARE_LAUNCHERS(float)
+PPML_DECLARE_LAUNCHERS(double)
+#undef PPML_DECLARE_LAUNCHERS
+
+}  // namespace ppml

@@ -115,6 +115,26 @@ def test_step_fp64_matches_oracle(case):
     assert d["steps"] == 3 and d["n_bad"] == 0
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_step_bitwise_equal_to_oracle(case):
+    """The FP64 kernels are built without FMA contraction and evaluate every expression in
+    the checker's order, so one step reproduces the oracle bit for bit."""
+    pb = CASES[case]()
+    g = oracle_grid(pb)
+    dt = oracle.cfl_dt(g, pb.u)
+    ref, _, ustar = oracle.step(g, pb.u, dt, want_star=True)
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    s = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.eulerian_stage(u, s, dt)
+    grid.step(u, v, dt)
+    got_s, got = host(s, shape_of(pb)), host(v, shape_of(pb))
+    diff_s = [int(np.count_nonzero(got_s[f] != ustar[f])) for f in range(6)]
+    diff = [int(np.count_nonzero(got[f] != ref[f])) for f in range(6)]
+    assert diff_s == [0] * 6 and diff == [0] * 6, (diff_s, diff)
+
+
 @pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_2d", "point_blast_16"])
 def test_step_fp32_single_step(case):
     """One FP32 step from the same (FP32-representable) input as the oracle."""
