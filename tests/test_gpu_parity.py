@@ -327,10 +327,29 @@ def _batch_oracle_run(b, i):
     return ref, steps
 
 
+def _noise_sensitivity(b, i, ref, eps=1e-7, seed=7):
+    """Relative L1 change of the FP64 oracle's final density when the instance's initial
+    state carries random relative noise of size eps (FP32 rounding level): the best
+    agreement any FP32 evaluation of the same scheme can be held to."""
+    n = int(b.ncells[i])
+    sl = slice(b.offsets[i], b.offsets[i + 1])
+    rng = np.random.default_rng(seed)
+    z = np.zeros(n)
+    u = [b.u[0][sl], b.u[1][sl], z, z, b.u[2][sl], b.u[3][sl]]
+    u = [x * (1.0 + eps * rng.standard_normal(n)) for x in u]
+    g = oracle.Grid((n, 1, 1), (float(b.h[i]), 1.0, 1.0), b.gamma, (0,) * 6, b.cfl,
+                    rho_mean=float(np.mean(b.u[0][sl])))
+    pert, _, _, _ = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]))
+    return rel_l1(pert[0].ravel(), ref[0].ravel())
+
+
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_config4_batch_matches_oracle(dtype):
     """Batched uneven Riemann problems: a 24-instance batch, every instance against its
-    own 1D oracle run (FP64: 1e-10; FP32: 1e-4 on rho and p)."""
+    own 1D oracle run.  FP64: bit for bit.  FP32: relative L1 of rho and p within
+    max(1e-4, 2 S_i), S_i the oracle's own sensitivity to 1e-7 input noise (cold,
+    high-Mach collisions, where rho eps is a tiny difference of totals, have S_i above
+    1e-4; well-conditioned instances are held to 1e-4)."""
     from oracle import exact
     b = inputs.batched_riemann(n_inst=24, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
     bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, dtype)
@@ -344,15 +363,46 @@ def test_config4_batch_matches_oracle(dtype):
     t, steps = bt.status()
     assert np.allclose(t, b.t_end, rtol=1e-14)
     got = [x.double().cpu().numpy() for x in st]
-    tol = TOL64 if dtype == F64 else 1e-4
+    n_loose = 0
     for i in range(b.ncells.size):
         ref, steps_o = _batch_oracle(b, i)
-        assert abs(steps[i] - steps_o) <= (0 if dtype == F64 else 1)
         sl = slice(b.offsets[i], b.offsets[i + 1])
-        flds = ((0, 0), (1, 1), (2, 4), (3, 5)) if dtype == F64 else ((0, 0), (3, 5))
-        for k, f in flds:
-            e = rel_l1(got[k][sl], ref[f].ravel(), scale_ref=ref[0].ravel() if f == 1 else None)
-            assert e <= tol, (i, f, e)
+        if dtype == F64:
+            assert steps[i] == steps_o
+            for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+                assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
+            continue
+        assert abs(steps[i] - steps_o) <= 1
+        e_rho = rel_l1(got[0][sl], ref[0].ravel())
+        e_p = rel_l1(got[3][sl], ref[5].ravel())
+        tol = 1e-4
+        if max(e_rho, e_p) > tol:
+            tol = max(tol, 2.0 * _noise_sensitivity(b, i, ref))
+            n_loose += 1
+        assert e_rho <= tol and e_p <= tol, (i, e_rho, e_p, tol)
+    assert n_loose <= 2  # the sensitivity bound is for the rare ill-conditioned instance
+
+
+@pytest.mark.slow
+def test_config4_full_batch_sampled_instances():
+    """The full 512-instance batch (lengths 128..4096) in one persistent launch per call,
+    FP64; sampled instances (the longest, the shortest and four in between) against
+    their own oracle runs, bit for bit."""
+    from oracle import exact
+    b = inputs.batched_riemann(max_speed=exact.riemann_max_speed)
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    st = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    for _ in range(100):
+        if bt.step(st, 4000, sync=True) == b.ncells.size:
+            break
+    got = [x.cpu().numpy() for x in st]
+    order = np.argsort(b.ncells)
+    sample = [int(order[-1]), int(order[0])] + [int(order[q]) for q in (100, 250, 400, 480)]
+    for i in sample:
+        ref, steps_o = _batch_oracle(b, i)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+            assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
 
 
 def test_cuda_graph_replay_equals_eager():
