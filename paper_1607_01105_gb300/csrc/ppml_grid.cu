@@ -2,9 +2,9 @@
 // grid (Kulikov & Vorobyov, arXiv:1607.01105, Sec. 1).
 //
 // Per step, on the caller's stream:
-//   eulerian_march     Sec. 1.1/1.2: PPML parabolas of v and p, acoustic face solve,
+//   eulerian_tile      Sec. 1.1/1.2: PPML parabolas of v and p, acoustic face solve,
 //                      unsplit update of m, rho E, rho eps -> U* (library scratch)
-//   lagrangian_march   Sec. 1.3/1.4: 9-point velocity template, Roe-weighted face velocity,
+//   lagrangian_tile    Sec. 1.3/1.4: 9-point velocity template, Roe-weighted face velocity,
 //                      upwind parabola fluxes of all six fields, unsplit update, energy
 //                      correction; per-CTA partial maxima and sums of U^{n+1}
 //   finalize_kernel    deterministic reduction of the partials -> device-resident CFL step
@@ -97,7 +97,7 @@ struct ppml_grid {
   void* ustar[6];  // [0] unused (rho is not changed by the Eulerian stage)
   Partial* partials;
   int nblk_march, nblk_diag, npartials;
-  int tiles_x, tiles_y, nchunks, kc;
+  int tiles_x, tiles_y, tiles_z;
   DevScalars* dev;
   double rho_mean, rho_vac, hmin, vol;
   // measurement hook: events around each kernel of a step
@@ -161,8 +161,6 @@ MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev)
   A.partials = g->partials;
   A.tiles_x = g->tiles_x;
   A.tiles_y = g->tiles_y;
-  A.nchunks = g->nchunks;
-  A.kc = g->kc;
   return A;
 }
 
@@ -237,15 +235,6 @@ int run_step(ppml_grid* g, const ppml_state* uin, ppml_state* uout, const T* phi
   return rc;
 }
 
-// z-chunk length of a march CTA: long enough to amortise the 4-plane pipeline warm-up,
-// short enough to give several waves of CTAs on 152 SMs.
-int choose_kc(int tiles, int nz) {
-  if (nz == 1) return 1;
-  int kc = 64;
-  while (kc > 16 && (long long)tiles * ((nz + kc - 1) / kc) < 8 * 152) kc /= 2;
-  return std::min(kc, nz);
-}
-
 }  // namespace
 
 extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, void* stream,
@@ -268,11 +257,10 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
   g->geom.nxy = (long long)d->nx * d->ny;
   g->geom.ncell = g->geom.nxy * d->nz;
   g->elt = d->dtype == PPML_F64 ? 8 : 4;
-  g->tiles_x = (d->nx + TX - 1) / TX;
-  g->tiles_y = (d->ny + TY - 1) / TY;
-  g->kc = choose_kc(g->tiles_x * g->tiles_y, d->nz);
-  g->nchunks = (d->nz + g->kc - 1) / g->kc;
-  g->nblk_march = g->tiles_x * g->tiles_y * g->nchunks;
+  g->tiles_x = (d->nx + TB - 1) / TB;
+  g->tiles_y = (d->ny + TB - 1) / TB;
+  g->tiles_z = (d->nz + TB - 1) / TB;
+  g->nblk_march = g->tiles_x * g->tiles_y * g->tiles_z;
   g->nblk_diag = (int)std::min<long long>((g->geom.ncell + NT - 1) / NT, 4 * 152);
   g->npartials = std::max(g->nblk_march, g->nblk_diag);
   g->hmin = INFINITY;

@@ -23,13 +23,13 @@ struct MinBlocks<double> {
 template <>
 int prepare_kernels<PPML_REAL>() {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  cudaError_t e = cudaFuncSetAttribute(lagrangian_march<PPML_REAL, MB>,
+  cudaError_t e = cudaFuncSetAttribute(lagrangian_tile<PPML_REAL, MB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(LagSmem<PPML_REAL>));
+                                       (int)sizeof(LagTileSmem<PPML_REAL>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eulerian_march<PPML_REAL, MB>,
+    e = cudaFuncSetAttribute(eulerian_tile<PPML_REAL, MB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(EulSmem<PPML_REAL>));
+                             (int)sizeof(EulTileSmem<PPML_REAL>));
   if (e != cudaSuccess) return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   return PPML_OK;
 }
@@ -37,15 +37,15 @@ int prepare_kernels<PPML_REAL>() {
 template <>
 int launch_eulerian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  eulerian_march<PPML_REAL, MB><<<nblk, NT, sizeof(EulSmem<PPML_REAL>), st>>>(A);
-  return ppml_check_launch("eulerian_march");
+  eulerian_tile<PPML_REAL, MB><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
+  return ppml_check_launch("eulerian_tile");
 }
 
 template <>
 int launch_lagrangian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  lagrangian_march<PPML_REAL, MB><<<nblk, NT, sizeof(LagSmem<PPML_REAL>), st>>>(A);
-  return ppml_check_launch("lagrangian_march");
+  lagrangian_tile<PPML_REAL, MB><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
+  return ppml_check_launch("lagrangian_tile");
 }
 
 template <>

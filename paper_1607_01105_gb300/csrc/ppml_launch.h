@@ -6,7 +6,7 @@
 #include <stddef.h>
 
 #include "ppml_batch.cuh"
-#include "ppml_march.cuh"
+#include "ppml_tile.cuh"
 
 namespace ppml {
 

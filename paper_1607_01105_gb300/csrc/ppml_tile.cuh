@@ -1,0 +1,438 @@
+// Tiled line-sweep kernels of one PPML step (Kulikov & Vorobyov, arXiv:1607.01105).
+//
+// A CTA of 256 threads owns a 16^3 tile.  Thread t = a + 16 b owns one line per axis
+// (x line (j, k) = (a, b); y line (i, k) = (a, b); z line (i, j) = (a, b)).  Each line is
+// swept by a fully unrolled register pipeline: when position p arrives, the limited slope
+// at p-1, the face value at p-3/2, the parabola of p-2 and the flux through the face
+// p-5/2 are formed (Appendix Steps 1-3, characteristic averages), so every quantity along
+// the line is computed once; the 3-cell halo costs 6 extra positions per 16 cells.
+// Data is staged in shared memory (Lagrangian: one field box with a 3-cell cross-shaped
+// halo; Eulerian: one slab per axis) with pitches that make every sweep's accesses
+// bank-conflict free in FP32.  Boundaries are index maps on every load; tiles away from
+// the domain faces take the unmapped fast path.  The unsplit sums over axes are taken in
+// the order x, y, z.
+#pragma once
+#include "ppml_common.cuh"
+
+namespace ppml {
+
+constexpr int TB = 16;           // tile edge
+constexpr int TN = TB * TB;      // threads per CTA = lines per axis
+constexpr int TH = 3;            // halo
+constexpr int TW = TB + 2 * TH;  // 22 positions per line
+// field box: (i, j, k) in [-3, 18]^3 (cross-shaped part used), pitches 23 and 528
+constexpr int BRP = 23, BPP = 528, BOX = TW * BPP;
+// accumulator over the tile: pitches 17 and 272
+constexpr int ARP = 17, APP = 272, ACC = TB * APP;
+// slab: position p in [-3, 18] times 256 transverse cells, pitch 257
+constexpr int SLP = TN + 1, SLAB = TW * SLP;
+
+__device__ __forceinline__ int box_at(int i, int j, int k) {
+  return (i + TH) + BRP * (j + TH) + BPP * (k + TH);
+}
+__device__ __forceinline__ int acc_at(int i, int j, int k) { return i + ARP * j + APP * k; }
+
+struct TileGeom {
+  int i0, j0, k0;
+  bool fast;  // every cell within 3 of the tile is inside the domain on active axes
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, int tiles_x, int tiles_y) {
+  TileGeom t;
+  int b = blockIdx.x;
+  t.i0 = (b % tiles_x) * TB;
+  b /= tiles_x;
+  t.j0 = (b % tiles_y) * TB;
+  t.k0 = (b / tiles_y) * TB;
+  const int o[3] = {t.i0, t.j0, t.k0};
+  bool f = true;
+  for (int a = 0; a < 3; a++) f = f && g.n[a] > 1 && o[a] - TH >= 0 && o[a] + TB + TH <= g.n[a];
+  t.fast = f;
+  return t;
+}
+
+// Linear index of tile-relative cell (i, j, k) and the reflection flags of its mapping.
+__device__ __forceinline__ long long cell_index(const GridGeom& g, const TileGeom& t, int i, int j,
+                                                int k, int fl[3]) {
+  if (t.fast) {
+    fl[0] = fl[1] = fl[2] = 0;
+    return (long long)(t.i0 + i) + (long long)g.n[0] * (t.j0 + j) + g.nxy * (t.k0 + k);
+  }
+  return map_cell(t.i0 + i, t.j0 + j, t.k0 + k, g, fl);
+}
+
+template <typename T>
+__device__ __forceinline__ T load_field(const T* __restrict__ q, int f, const GridGeom& g,
+                                        const TileGeom& t, int i, int j, int k) {
+  int fl[3];
+  T v = q[cell_index(g, t, i, j, k, fl)];
+  if ((f == 1 && fl[0]) || (f == 2 && fl[1]) || (f == 3 && fl[2])) v = -v;
+  return v;
+}
+
+__device__ __forceinline__ bool in_domain(const GridGeom& g, const TileGeom& t, int i, int j,
+                                          int k) {
+  return t.i0 + i < g.n[0] && t.j0 + j < g.n[1] && t.k0 + k < g.n[2];
+}
+
+// Tile-relative coordinates of position p on the line (a, b) of axis ax.
+__device__ __forceinline__ void line_cell(int ax, int p, int a, int b, int& i, int& j, int& k) {
+  i = ax == 0 ? p : a;
+  j = ax == 0 ? a : (ax == 1 ? p : b);
+  k = ax == 2 ? p : b;
+}
+
+// ---------------------------------------------------------------- line pipelines
+
+// Lagrangian sweep of one field along one line.  q(p) returns the field at position p in
+// [-3, 18]; vh(c) is the face velocity between cells c-1 and c (c = 0..16).  emit(c, d) is
+// called for c = 0..15 with d = th * (F(c+1/2) - F(c-1/2)).
+template <typename T, typename QF, typename VF, typename EF>
+__device__ __forceinline__ void sweep_lagrangian(QF q, VF vh, T th, double tau, double h,
+                                                 EF emit) {
+  T qa = q(-3), qb = q(-2);  // q(p-2), q(p-1)
+  T da = T(0), fa = T(0);    // slope(p-2), face(p-5/2)
+  T PR = T(0), PD = T(0), PS = T(0), Fp = T(0);
+#pragma unroll
+  for (int p = -1; p <= TB + 2; p++) {
+    const T qn = q(p);
+    const T dn = limited_slope(qa, qb, qn);  // slope(p-1)
+    T fn = T(0);
+    if (p >= 0) fn = face_value(qa, qb, da, dn);  // face(p-3/2)
+    if (p >= 1) {
+      const Parab<T> P = parabola(qa, fa, fn);  // cell p-2
+      if (p >= 2) {
+        const T v = vh(p - 2);  // face between cells p-3 and p-2
+        const T y = Prec<T>::courant(tabs(v), tau, h, th);
+        const T F = v >= T(0) ? v * avg_right(PR, PD, PS, y) : v * avg_left(P.L, P.D, P.S, y);
+        if (p >= 3) emit(p - 3, th * (F - Fp));
+        Fp = F;
+      }
+      PR = P.R;
+      PD = P.D;
+      PS = P.S;
+    }
+    qa = qb;
+    qb = qn;
+    da = dn;
+    fa = fn;
+  }
+}
+
+// Eulerian sweep along one line: v(p), pr(p), r(p) give v_a, p and rho at position p.
+// emit(c, dm, dpv, dv) is called for cells c = 0..15 with dm = th (P+ - P-),
+// dpv = th (P+V+ - P-V-), dv = th (V+ - V-).
+template <typename T, typename VF, typename PF, typename RF, typename EF>
+__device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th, double tau,
+                                               double h, EF emit) {
+  T va = v(-3), vb = v(-2), pa = pr(-3), pb = pr(-2);
+  T dva = T(0), fva = T(0), dpa = T(0), fpa = T(0);
+  T vR = T(0), vD = T(0), vS = T(0), pR = T(0), pD = T(0), pS = T(0);
+  T Vp = T(0), Pp = T(0);
+  T rprev = T(0), pprev = T(0);  // rho, p of cell p-3
+#pragma unroll
+  for (int p = -1; p <= TB + 2; p++) {
+    const T vn = v(p), pn = pr(p);
+    const T dvn = limited_slope(va, vb, vn), dpn = limited_slope(pa, pb, pn);
+    T fvn = T(0), fpn = T(0);
+    if (p >= 0) {
+      fvn = face_value(va, vb, dva, dvn);
+      fpn = face_value(pa, pb, dpa, dpn);
+    }
+    if (p >= 1) {
+      const Parab<T> Pv = parabola(va, fva, fvn);  // cell p-2
+      const Parab<T> Pq = parabola(pa, fpa, fpn);
+      const T rc = r(p - 2);
+      if (p >= 2) {
+        // face between cells p-3 and p-2
+        T lam, Z;
+        face_constants(rprev, rc, pprev, pa, gamma, lam, Z);
+        const T y = Prec<T>::courant(lam, tau, h, th);
+        T V, P;
+        riemann_vp(avg_right(vR, vD, vS, y), avg_left(Pv.L, Pv.D, Pv.S, y),
+                   avg_right(pR, pD, pS, y), avg_left(Pq.L, Pq.D, Pq.S, y), Z, V, P);
+        if (p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
+        Vp = V;
+        Pp = P;
+      }
+      vR = Pv.R;
+      vD = Pv.D;
+      vS = Pv.S;
+      pR = Pq.R;
+      pD = Pq.D;
+      pS = Pq.S;
+      rprev = rc;
+      pprev = pa;
+    }
+    va = vb;
+    vb = vn;
+    dva = dvn;
+    fva = fvn;
+    pa = pb;
+    pb = pn;
+    dpa = dpn;
+    fpa = fpn;
+  }
+}
+
+// ===================================================================== Lagrangian stage
+
+template <typename T>
+struct LagTileSmem {
+  T box[BOX];              // one field of U* (or v_a for the template) around the tile
+  T acc[ACC];              // x + y part of the flux divergence
+  T vh[2][TB + 1][TN];     // face velocities of the x and y lines, [face][line]
+};
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LagTileSmem<T>& S = *reinterpret_cast<LagTileSmem<T>*>(smem_raw);
+  const GridGeom& g = A.g;
+  const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
+  const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
+  const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const double tau = read_tau(A.dt_dev, A.dt_host);
+  const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
+  const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
+
+  // ---- face velocities of the three lines of this thread (eqs. veltemplate,
+  //      modspaceaveragevelocitylagrange), kept for all six fields: x and y lines in
+  //      shared memory, the z line in registers
+  T vhz[TB + 1];
+#pragma unroll
+  for (int ax = 0; ax < 3; ax++) {
+    if (!act[ax]) continue;
+    // v_ax = m_ax / rho over [-1, 16]^3
+    for (int it = tid; it < 18 * 18 * 18; it += TN) {
+      const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
+      int fl[3];
+      const long long c = cell_index(g, tg, i, j, k, fl);
+      T m = A.u[1 + ax][c];
+      if (fl[ax]) m = -m;
+      S.box[box_at(i, j, k)] = m / A.u[0][c];
+    }
+    __syncthreads();
+    // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
+    T vt_prev = T(0), sq_prev = T(0);
+#pragma unroll
+    for (int p = -1; p <= TB; p++) {
+      int i, j, k;
+      line_cell(ax, p, a, b, i, j, k);
+      int di1 = 0, dj1 = 0, dk1 = 0, di2 = 0, dj2 = 0, dk2 = 0;  // role b, role c offsets
+      if (ax == 0) { dj1 = 1; dk2 = 1; }
+      if (ax == 1) { dk1 = 1; di2 = 1; }
+      if (ax == 2) { di1 = 1; dj2 = 1; }
+      auto V = [&](int sb, int sc) {
+        return S.box[box_at(i + sb * di1 + sc * di2, j + sb * dj1 + sc * dj2, k + sb * dk1 + sc * dk2)];
+      };
+      const T corners = V(1, 1) + V(1, -1) + V(-1, 1) + V(-1, -1);
+      const T edges = V(1, 0) + V(-1, 0) + V(0, 1) + V(0, -1);
+      const T vt = corners / T(16) + edges / T(8) + V(0, 0) / T(4);
+      int fl[3];
+      const T sq = sqrt(A.u[0][cell_index(g, tg, i, j, k, fl)]);
+      if (p >= 0) {
+        const T v = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
+        if (ax == 2)
+          vhz[p] = v;
+        else
+          S.vh[ax][p][tid] = v;
+      }
+      vt_prev = vt;
+      sq_prev = sq;
+    }
+    __syncthreads();
+  }
+
+  // ---- per field: stage the box, sweep x, y (into acc), z (finish), store
+#pragma unroll 1
+  for (int f = 0; f < 6; f++) {
+    const T* __restrict__ src = A.u[f];
+    for (int it = tid; it < TB * TB * TB; it += TN) {  // interior
+      const int i = it % TB, j = (it / TB) % TB, k = it / TN;
+      S.box[box_at(i, j, k)] = load_field(src, f, g, tg, i, j, k);
+    }
+    for (int it = tid; it < 3 * 6 * TN; it += TN) {  // halo slabs of each active axis
+      const int ax = it / (6 * TN), r = it % (6 * TN);
+      if (!act[ax]) continue;
+      const int h = r / TN, s = r % TN;  // h in 0..5: positions -3..-1, 16..18
+      const int p = h < 3 ? h - 3 : TB + h - 3;
+      int i, j, k;
+      if (ax == 0) { i = p; j = s % TB; k = s / TB; }
+      else if (ax == 1) { i = s % TB; j = p; k = s / TB; }
+      else { i = s % TB; j = s / TB; k = p; }
+      S.box[box_at(i, j, k)] = load_field(src, f, g, tg, i, j, k);
+    }
+    __syncthreads();
+    bool first = true;
+#pragma unroll
+    for (int ax = 0; ax < 2; ax++) {
+      if (!act[ax]) continue;
+      auto emit = [&](int c, T d) {
+        const int ai = ax == 0 ? acc_at(c, a, b) : acc_at(a, c, b);
+        S.acc[ai] = first ? d : S.acc[ai] + d;
+      };
+      auto vhl = [&](int c) { return S.vh[ax][c][tid]; };
+      if (ax == 0)
+        sweep_lagrangian<T>([&](int p) { return S.box[box_at(p, a, b)]; }, vhl, th[0], tau,
+                            A.h[0], emit);
+      else
+        sweep_lagrangian<T>([&](int p) { return S.box[box_at(a, p, b)]; }, vhl, th[1], tau,
+                            A.h[1], emit);
+      first = false;
+      __syncthreads();
+    }
+    T* __restrict__ dst = A.out[f];
+    const long long line0 = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
+    auto finish = [&](int c, T dz) {
+      if (!in_domain(g, tg, a, b, c)) return;
+      T d = first ? T(0) : S.acc[acc_at(a, b, c)];
+      if (act[2]) d = first ? dz : d + dz;
+      dst[line0 + g.nxy * c] = S.box[box_at(a, b, c)] - d;
+    };
+    if (act[2])
+      sweep_lagrangian<T>([&](int p) { return S.box[box_at(a, b, p)]; },
+                          [&](int c) { return vhz[c]; }, th[2], tau, A.h[2], finish);
+    else
+      for (int c = 0; c < TB; c++) finish(c, T(0));
+    __syncthreads();
+  }
+
+  // ---- energy correction (Sec. 1.4), CFL maxima and sums of the thread's z line
+  FieldSums<T> sums;
+  sums.init();
+  T vmax = T(0), cmax = T(0);
+  unsigned long long nvac = 0, nbad = 0;
+  for (int c = 0; c < TB; c++) {
+    if (!in_domain(g, tg, a, b, c)) continue;
+    const long long idx = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * (tg.k0 + c);
+    T u[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) u[f] = A.out[f][idx];
+    nvac += correct_energy<T>(u, A.rho_vac);
+    A.out[1][idx] = u[1];
+    A.out[2][idx] = u[2];
+    A.out[3][idx] = u[3];
+    A.out[5][idx] = u[5];
+    sums.add(u);
+    cell_speeds<T>(u, gamma, gm1, vmax, cmax, nbad);
+  }
+  double sd[6];
+  sums.get(sd);
+  block_reduce_store<TN>(sd, (double)vmax, (double)cmax, nvac, nbad, A.partials);
+}
+
+// ====================================================================== Eulerian stage
+
+template <typename T>
+struct EulTileSmem {
+  T r[SLAB];   // rho along the sweep axis
+  T m[SLAB];   // m_a along the sweep axis
+  T p[SLAB];   // p along the sweep axis
+  T apv[ACC];  // sum over axes of th (PV+ - PV-)
+  T av[ACC];   // sum over axes of th (V+ - V-)
+};
+
+__device__ __forceinline__ int slab_at(int p, int a, int b) { return (p + TH) * SLP + a + TB * b; }
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EulTileSmem<T>& S = *reinterpret_cast<EulTileSmem<T>*>(smem_raw);
+  const GridGeom& g = A.g;
+  const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
+  const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
+  const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const double tau = read_tau(A.dt_dev, A.dt_host);
+  const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
+  const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
+
+  bool first = true;
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ax++) {
+    if (!act[ax]) continue;
+    // stage rho, m_ax, p along the axis: position p in [-3, 18], transverse (s % 16, s / 16)
+    for (int it = tid; it < TW * TN; it += TN) {
+      int p, s;
+      if (ax == 0) {  // x fastest in memory: walk p fastest
+        p = it % TW - TH;
+        s = it / TW;
+      } else {
+        s = it % TN;
+        p = it / TN - TH;
+      }
+      int i, j, k;
+      line_cell(ax, p, s % TB, s / TB, i, j, k);
+      int fl[3];
+      const long long c = cell_index(g, tg, i, j, k, fl);
+      T m = A.u[1 + ax][c];
+      if (fl[ax]) m = -m;
+      const int o = slab_at(p, s % TB, s / TB);
+      S.r[o] = A.u[0][c];
+      S.m[o] = m;
+      S.p[o] = gm1 * A.u[5][c];
+    }
+    __syncthreads();
+    auto emit = [&](int c, T dm, T dpv, T dv) {
+      int i, j, k;
+      line_cell(ax, c, a, b, i, j, k);
+      const int ai = acc_at(i, j, k);
+      S.apv[ai] = first ? dpv : S.apv[ai] + dpv;
+      S.av[ai] = first ? dv : S.av[ai] + dv;
+      if (in_domain(g, tg, i, j, k)) {
+        const long long idx = (long long)(tg.i0 + i) + (long long)g.n[0] * (tg.j0 + j) + g.nxy * (tg.k0 + k);
+        A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
+      }
+    };
+    sweep_eulerian<T>([&](int p) { const int o = slab_at(p, a, b); return S.m[o] / S.r[o]; },
+                      [&](int p) { return S.p[slab_at(p, a, b)]; },
+                      [&](int p) { return S.r[slab_at(p, a, b)]; }, gamma, th[ax], tau, A.h[ax],
+                      emit);
+    first = false;
+    __syncthreads();
+  }
+  // momentum of inactive axes is unchanged
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ax++) {
+    if (act[ax]) continue;
+    for (int c = 0; c < TB; c++) {
+      if (!in_domain(g, tg, a, b, c)) continue;
+      const long long idx = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * (tg.k0 + c);
+      A.out[1 + ax][idx] = A.u[1 + ax][idx];
+    }
+  }
+  __syncthreads();
+  // rho E, rho eps (and the optional gravity source), cells of the thread's z line
+  for (int c = 0; c < TB; c++) {
+    if (!in_domain(g, tg, a, b, c)) continue;
+    const int gi = tg.i0 + a, gj = tg.j0 + b, gk = tg.k0 + c;
+    const long long idx = (long long)gi + (long long)g.n[0] * gj + g.nxy * gk;
+    const T rho0 = A.u[0][idx];
+    const T ei0 = A.u[5][idx];
+    const T dpvs = first ? T(0) : S.apv[acc_at(a, b, c)];
+    const T dvs = first ? T(0) : S.av[acc_at(a, b, c)];
+    T en = A.u[4][idx] - dpvs;
+    if (A.phi) {
+      T m[3] = {A.out[1][idx], A.out[2][idx], A.out[3][idx]};
+      const T m0[3] = {A.u[1][idx], A.u[2][idx], A.u[3][idx]};
+#pragma unroll 1
+      for (int ax = 0; ax < 3; ax++) {
+        if (!act[ax]) continue;
+        const int di = ax == 0, dj = ax == 1, dk = ax == 2;
+        const T pp = load_bc(A.phi, -1, gi + di, gj + dj, gk + dk, g);
+        const T pm = load_bc(A.phi, -1, gi - di, gj - dj, gk - dk, g);
+        const T grad = (pp - pm) / T(2.0 * A.h[ax]);
+        m[ax] -= T(tau) * rho0 * grad;
+        en -= T(tau) * m0[ax] * grad;
+      }
+      A.out[1][idx] = m[0];
+      A.out[2][idx] = m[1];
+      A.out[3][idx] = m[2];
+    }
+    if (A.out[0]) A.out[0][idx] = rho0;
+    A.out[4][idx] = en;
+    A.out[5][idx] = ei0 - gm1 * ei0 * dvs;
+  }
+}
+
+}  // namespace ppml
