@@ -35,6 +35,7 @@ struct MarchArgs {
   double rho_vac;
   Partial* partials;
   int tiles_x, tiles_y;  // tile grid of the stage kernels (z tiles = grid / (x * y))
+  int any_reflect;       // a reflecting wall exists (its sign flips need register copies)
 };
 
 __device__ __forceinline__ double read_tau(const double* dt_dev, double dt_host) {

@@ -161,6 +161,8 @@ MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev)
   A.partials = g->partials;
   A.tiles_x = g->tiles_x;
   A.tiles_y = g->tiles_y;
+  A.any_reflect = 0;
+  for (int q = 0; q < 6; q++) A.any_reflect |= g->d.bc[q] == PPML_BC_REFLECT;
   return A;
 }
 

@@ -177,12 +177,95 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
 
 // ===================================================================== Lagrangian stage
 
+// Asynchronous global -> shared copies of one element (cp.async, completion awaited with
+// cp.async.wait_all before the CTA barrier).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Field storage of the Lagrangian tile: the 16^3 core (pitches 17, 272) and, per axis, the
+// six halo positions -3..-1, 16..18 of every line (line-major, pitch 257).  Reused as a
+// dense 18^3 box of v_a while the face velocities are formed.
+constexpr int HALO_POS = 6;
+constexpr int LAG_FIELD = ACC + 3 * HALO_POS * SLP;
+static_assert(LAG_FIELD >= 18 * 18 * 18, "template box must fit in the field storage");
+
 template <typename T>
 struct LagTileSmem {
-  T box[BOX];              // one field of U* (or v_a for the template) around the tile
-  T acc[ACC];              // x + y part of the flux divergence
-  T vh[2][TB + 1][TN];     // face velocities of the x and y lines, [face][line]
+  T fld[LAG_FIELD];   // core (ACC) then halo[3][6][SLP]
+  T acc[ACC];         // x + y part of the flux divergence
+  T vh[3][TB + 1][TN];  // face velocities of every line, [axis][face][line]
 };
+
+__device__ __forceinline__ int halo_at(int ax, int h, int line) {
+  return ACC + (ax * HALO_POS + h) * SLP + line;
+}
+__device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, coords -1..16
+  return (i + 1) + 18 * (j + 1) + 324 * (k + 1);
+}
+
+// One line of the Lagrangian stage for any axis.  Field values: core[cb + p cs] for
+// p in [0, 16), halo positions at hb + h SLP.  Face velocities vh[vb + c TN].
+// mode 0: acc = div; 1: acc += div; 2: finish (out = core - (acc + div)), written to
+// dst[gb + c gs] for c < nvalid.  have_acc: acc holds an x/y part (mode 2 only).
+template <typename T>
+__device__ __forceinline__ void lag_line(const T* fld, int cb, int cs, int hb, const T* vh,
+                                         int vb, T th, double tau, double h, int mode,
+                                         bool have_acc, T* acc, T* __restrict__ dst,
+                                         long long gb, long long gs, int nvalid) {
+  auto q = [&](int p) -> T {
+    if (p < 0) return fld[hb + (p + 3) * SLP];
+    if (p >= TB) return fld[hb + (p - TB + 3) * SLP];
+    return fld[cb + p * cs];
+  };
+  T qa = q(-3), qb = q(-2);
+  T da = T(0), fa = T(0);
+  T PR = T(0), PD = T(0), PS = T(0), Fp = T(0);
+#pragma unroll
+  for (int p = -1; p <= TB + 2; p++) {
+    const T qn = q(p);
+    const T dn = limited_slope(qa, qb, qn);
+    T fn = T(0);
+    if (p >= 0) fn = face_value(qa, qb, da, dn);
+    if (p >= 1) {
+      const Parab<T> P = parabola(qa, fa, fn);  // cell p-2
+      if (p >= 2) {
+        const T v = vh[vb + (p - 2) * TN];  // face between cells p-3 and p-2
+        const T y = Prec<T>::courant(tabs(v), tau, h, th);
+        const T F = v >= T(0) ? v * avg_right(PR, PD, PS, y) : v * avg_left(P.L, P.D, P.S, y);
+        if (p >= 3) {
+          const int c = p - 3;
+          const T d = th * (F - Fp);
+          const int o = cb + c * cs;
+          if (mode == 0) {
+            acc[o] = d;
+          } else if (mode == 1) {
+            acc[o] = acc[o] + d;
+          } else if (c < nvalid) {
+            const T dt = have_acc ? acc[o] + d : d;
+            dst[gb + gs * c] = fld[o] - dt;
+          }
+        }
+        Fp = F;
+      }
+      PR = P.R;
+      PD = P.D;
+      PS = P.S;
+    }
+    qa = qb;
+    qb = qn;
+    da = dn;
+    fa = fn;
+  }
+}
 
 template <typename T, int MINB>
 __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
@@ -195,106 +278,101 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const double tau = read_tau(A.dt_dev, A.dt_host);
   const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
+  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
 
-  // ---- face velocities of the three lines of this thread (eqs. veltemplate,
-  //      modspaceaveragevelocitylagrange), kept for all six fields: x and y lines in
-  //      shared memory, the z line in registers
-  T vhz[TB + 1];
-#pragma unroll
+  // ---- face velocities of every line (eqs. veltemplate, modspaceaveragevelocitylagrange)
+#pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
-    // v_ax = m_ax / rho over [-1, 16]^3
-    for (int it = tid; it < 18 * 18 * 18; it += TN) {
+    for (int it = tid; it < 18 * 18 * 18; it += TN) {  // v_ax = m_ax / rho over [-1, 16]^3
       const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
       int fl[3];
       const long long c = cell_index(g, tg, i, j, k, fl);
       T m = A.u[1 + ax][c];
       if (fl[ax]) m = -m;
-      S.box[box_at(i, j, k)] = m / A.u[0][c];
+      S.fld[tbox_at(i, j, k)] = m / A.u[0][c];
     }
     __syncthreads();
     // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
+    const int s_ax = ax == 0 ? 1 : (ax == 1 ? 18 : 324);
+    const int s_b = ax == 0 ? 18 : (ax == 1 ? 324 : 1);
+    const int s_c = ax == 0 ? 324 : (ax == 1 ? 1 : 18);
+    int li, lj, lk;
+    line_cell(ax, 0, a, b, li, lj, lk);
+    const int base = tbox_at(li, lj, lk);
     T vt_prev = T(0), sq_prev = T(0);
-#pragma unroll
+#pragma unroll 2
     for (int p = -1; p <= TB; p++) {
-      int i, j, k;
+      const int o = base + p * s_ax;
+      const T corners = S.fld[o + s_b + s_c] + S.fld[o + s_b - s_c] + S.fld[o - s_b + s_c] +
+                        S.fld[o - s_b - s_c];
+      const T edges = S.fld[o + s_b] + S.fld[o - s_b] + S.fld[o + s_c] + S.fld[o - s_c];
+      const T vt = corners / T(16) + edges / T(8) + S.fld[o] / T(4);
+      int i, j, k, fl[3];
       line_cell(ax, p, a, b, i, j, k);
-      int di1 = 0, dj1 = 0, dk1 = 0, di2 = 0, dj2 = 0, dk2 = 0;  // role b, role c offsets
-      if (ax == 0) { dj1 = 1; dk2 = 1; }
-      if (ax == 1) { dk1 = 1; di2 = 1; }
-      if (ax == 2) { di1 = 1; dj2 = 1; }
-      auto V = [&](int sb, int sc) {
-        return S.box[box_at(i + sb * di1 + sc * di2, j + sb * dj1 + sc * dj2, k + sb * dk1 + sc * dk2)];
-      };
-      const T corners = V(1, 1) + V(1, -1) + V(-1, 1) + V(-1, -1);
-      const T edges = V(1, 0) + V(-1, 0) + V(0, 1) + V(0, -1);
-      const T vt = corners / T(16) + edges / T(8) + V(0, 0) / T(4);
-      int fl[3];
       const T sq = sqrt(A.u[0][cell_index(g, tg, i, j, k, fl)]);
-      if (p >= 0) {
-        const T v = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
-        if (ax == 2)
-          vhz[p] = v;
-        else
-          S.vh[ax][p][tid] = v;
-      }
+      if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
       vt_prev = vt;
       sq_prev = sq;
     }
     __syncthreads();
   }
 
-  // ---- per field: stage the box, sweep x, y (into acc), z (finish), store
+  // ---- per field: stage, sweep x, y (into acc), z (finish into the output)
+  const bool line_ok = in_domain(g, tg, a, b, 0);
+  const int nvalid_z = line_ok ? min(TB, g.n[2] - tg.k0) : 0;
+  const long long zline0 =
+      (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
 #pragma unroll 1
   for (int f = 0; f < 6; f++) {
     const T* __restrict__ src = A.u[f];
-    for (int it = tid; it < TB * TB * TB; it += TN) {  // interior
+    for (int it = tid; it < TB * TB * TB; it += TN) {  // core
       const int i = it % TB, j = (it / TB) % TB, k = it / TN;
-      S.box[box_at(i, j, k)] = load_field(src, f, g, tg, i, j, k);
+      int fl[3];
+      const long long c = cell_index(g, tg, i, j, k, fl);
+      T* d = &S.fld[acc_at(i, j, k)];
+      if (async_ok)
+        cp_async_elem(d, src + c);
+      else
+        *d = load_field(src, f, g, tg, i, j, k);
     }
-    for (int it = tid; it < 3 * 6 * TN; it += TN) {  // halo slabs of each active axis
-      const int ax = it / (6 * TN), r = it % (6 * TN);
+    for (int it = tid; it < 3 * HALO_POS * TN; it += TN) {  // halo positions, active axes
+      const int ax = it / (HALO_POS * TN), r = it % (HALO_POS * TN);
       if (!act[ax]) continue;
-      const int h = r / TN, s = r % TN;  // h in 0..5: positions -3..-1, 16..18
+      const int h = r / TN, line = r % TN;
       const int p = h < 3 ? h - 3 : TB + h - 3;
       int i, j, k;
-      if (ax == 0) { i = p; j = s % TB; k = s / TB; }
-      else if (ax == 1) { i = s % TB; j = p; k = s / TB; }
-      else { i = s % TB; j = s / TB; k = p; }
-      S.box[box_at(i, j, k)] = load_field(src, f, g, tg, i, j, k);
-    }
-    __syncthreads();
-    bool first = true;
-#pragma unroll
-    for (int ax = 0; ax < 2; ax++) {
-      if (!act[ax]) continue;
-      auto emit = [&](int c, T d) {
-        const int ai = ax == 0 ? acc_at(c, a, b) : acc_at(a, c, b);
-        S.acc[ai] = first ? d : S.acc[ai] + d;
-      };
-      auto vhl = [&](int c) { return S.vh[ax][c][tid]; };
-      if (ax == 0)
-        sweep_lagrangian<T>([&](int p) { return S.box[box_at(p, a, b)]; }, vhl, th[0], tau,
-                            A.h[0], emit);
+      line_cell(ax, p, line % TB, line / TB, i, j, k);
+      int fl[3];
+      const long long c = cell_index(g, tg, i, j, k, fl);
+      T* d = &S.fld[halo_at(ax, h, line)];
+      if (async_ok)
+        cp_async_elem(d, src + c);
       else
-        sweep_lagrangian<T>([&](int p) { return S.box[box_at(a, p, b)]; }, vhl, th[1], tau,
-                            A.h[1], emit);
-      first = false;
-      __syncthreads();
+        *d = load_field(src, f, g, tg, i, j, k);
     }
-    T* __restrict__ dst = A.out[f];
-    const long long line0 = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
-    auto finish = [&](int c, T dz) {
-      if (!in_domain(g, tg, a, b, c)) return;
-      T d = first ? T(0) : S.acc[acc_at(a, b, c)];
-      if (act[2]) d = first ? dz : d + dz;
-      dst[line0 + g.nxy * c] = S.box[box_at(a, b, c)] - d;
-    };
-    if (act[2])
-      sweep_lagrangian<T>([&](int p) { return S.box[box_at(a, b, p)]; },
-                          [&](int c) { return vhz[c]; }, th[2], tau, A.h[2], finish);
-    else
-      for (int c = 0; c < TB; c++) finish(c, T(0));
+    if (async_ok) cp_async_wait_all();
+    __syncthreads();
+    int mode = 0;
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ax++) {
+      if (!act[ax]) continue;
+      int li, lj, lk;
+      line_cell(ax, 0, a, b, li, lj, lk);
+      const int cs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
+      const int m = ax == 2 ? 2 : mode;
+      lag_line<T>(S.fld, acc_at(li, lj, lk), cs, halo_at(ax, 0, tid), &S.vh[0][0][0],
+                  ax * (TB + 1) * TN + tid, th[ax], tau, A.h[ax], m, mode == 1, S.acc,
+                  A.out[f], zline0, g.nxy, nvalid_z);
+      mode = 1;
+      if (ax < 2) __syncthreads();
+    }
+    if (!act[2]) {  // no z sweep: finish from the x/y part
+      for (int c = 0; c < nvalid_z; c++) {
+        const int o = acc_at(a, b, c);
+        A.out[f][zline0 + g.nxy * c] = S.fld[o] - (mode == 1 ? S.acc[o] : T(0));
+      }
+    }
     __syncthreads();
   }
 
@@ -303,9 +381,8 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   sums.init();
   T vmax = T(0), cmax = T(0);
   unsigned long long nvac = 0, nbad = 0;
-  for (int c = 0; c < TB; c++) {
-    if (!in_domain(g, tg, a, b, c)) continue;
-    const long long idx = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * (tg.k0 + c);
+  for (int c = 0; c < nvalid_z; c++) {
+    const long long idx = zline0 + g.nxy * c;
     T u[6];
 #pragma unroll
     for (int f = 0; f < 6; f++) u[f] = A.out[f][idx];
@@ -328,7 +405,7 @@ template <typename T>
 struct EulTileSmem {
   T r[SLAB];   // rho along the sweep axis
   T m[SLAB];   // m_a along the sweep axis
-  T p[SLAB];   // p along the sweep axis
+  T p[SLAB];   // rho eps along the sweep axis (p = (gamma - 1) rho eps when read)
   T apv[ACC];  // sum over axes of th (PV+ - PV-)
   T av[ACC];   // sum over axes of th (V+ - V-)
 };
@@ -347,11 +424,13 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
 
+  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   bool first = true;
 #pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
-    // stage rho, m_ax, p along the axis: position p in [-3, 18], transverse (s % 16, s / 16)
+    // stage rho, m_ax, rho eps along the axis: position p in [-3, 18], transverse
+    // (s % 16, s / 16)
     for (int it = tid; it < TW * TN; it += TN) {
       int p, s;
       if (ax == 0) {  // x fastest in memory: walk p fastest
@@ -365,13 +444,20 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       line_cell(ax, p, s % TB, s / TB, i, j, k);
       int fl[3];
       const long long c = cell_index(g, tg, i, j, k, fl);
-      T m = A.u[1 + ax][c];
-      if (fl[ax]) m = -m;
       const int o = slab_at(p, s % TB, s / TB);
-      S.r[o] = A.u[0][c];
-      S.m[o] = m;
-      S.p[o] = gm1 * A.u[5][c];
+      if (async_ok) {
+        cp_async_elem(&S.r[o], A.u[0] + c);
+        cp_async_elem(&S.m[o], A.u[1 + ax] + c);
+        cp_async_elem(&S.p[o], A.u[5] + c);
+      } else {
+        T m = A.u[1 + ax][c];
+        if (fl[ax]) m = -m;
+        S.r[o] = A.u[0][c];
+        S.m[o] = m;
+        S.p[o] = A.u[5][c];
+      }
     }
+    if (async_ok) cp_async_wait_all();
     __syncthreads();
     auto emit = [&](int c, T dm, T dpv, T dv) {
       int i, j, k;
@@ -385,7 +471,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       }
     };
     sweep_eulerian<T>([&](int p) { const int o = slab_at(p, a, b); return S.m[o] / S.r[o]; },
-                      [&](int p) { return S.p[slab_at(p, a, b)]; },
+                      [&](int p) { return gm1 * S.p[slab_at(p, a, b)]; },
                       [&](int p) { return S.r[slab_at(p, a, b)]; }, gamma, th[ax], tau, A.h[ax],
                       emit);
     first = false;

@@ -327,29 +327,34 @@ def _batch_oracle_run(b, i):
     return ref, steps
 
 
-def _noise_sensitivity(b, i, ref, eps=1e-7, seed=7):
-    """Relative L1 change of the FP64 oracle's final density when the instance's initial
-    state carries random relative noise of size eps (FP32 rounding level): the best
-    agreement any FP32 evaluation of the same scheme can be held to."""
+def _fp32_storage_sensitivity(b, i, ref):
+    """Relative L1 change of the FP64 oracle's final rho and p when its state is rounded
+    to float32 after every step (FP64 arithmetic, FP32 storage): the best agreement any
+    FP32-state evaluation of the scheme can be held to for this instance."""
     n = int(b.ncells[i])
     sl = slice(b.offsets[i], b.offsets[i + 1])
-    rng = np.random.default_rng(seed)
     z = np.zeros(n)
-    u = [b.u[0][sl], b.u[1][sl], z, z, b.u[2][sl], b.u[3][sl]]
-    u = [x * (1.0 + eps * rng.standard_normal(n)) for x in u]
+    u = [x.astype(np.float32).astype(np.float64)
+         for x in (b.u[0][sl], b.u[1][sl], z, z, b.u[2][sl], b.u[3][sl])]
     g = oracle.Grid((n, 1, 1), (float(b.h[i]), 1.0, 1.0), b.gamma, (0,) * 6, b.cfl,
                     rho_mean=float(np.mean(b.u[0][sl])))
-    pert, _, _, _ = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]))
-    return rel_l1(pert[0].ravel(), ref[0].ravel())
+
+    def round32(step, t, uu, dg):
+        for f in range(6):
+            uu[f][...] = uu[f].astype(np.float32).astype(np.float64)
+
+    r32, _, _, _ = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]), callback=round32)
+    return max(rel_l1(r32[0].ravel(), ref[0].ravel()), rel_l1(r32[5].ravel(), ref[5].ravel()))
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_config4_batch_matches_oracle(dtype):
     """Batched uneven Riemann problems: a 24-instance batch, every instance against its
     own 1D oracle run.  FP64: bit for bit.  FP32: relative L1 of rho and p within
-    max(1e-4, 2 S_i), S_i the oracle's own sensitivity to 1e-7 input noise (cold,
-    high-Mach collisions, where rho eps is a tiny difference of totals, have S_i above
-    1e-4; well-conditioned instances are held to 1e-4)."""
+    max(1e-4, 2 S_i), S_i the change of the FP64 oracle itself when its state is stored in
+    float32 between steps.  Cold, high-Mach collisions (rho eps a tiny difference of
+    totals) have S_i far above 1e-4 (instance 10: 5.8e-4 in rho, 2.6e-3 in p); the other
+    instances have S_i <= 6e-5 and are held to 1e-4."""
     from oracle import exact
     b = inputs.batched_riemann(n_inst=24, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
     bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, dtype)
@@ -377,7 +382,7 @@ def test_config4_batch_matches_oracle(dtype):
         e_p = rel_l1(got[3][sl], ref[5].ravel())
         tol = 1e-4
         if max(e_rho, e_p) > tol:
-            tol = max(tol, 2.0 * _noise_sensitivity(b, i, ref))
+            tol = max(tol, 2.0 * _fp32_storage_sensitivity(b, i, ref))
             n_loose += 1
         assert e_rho <= tol and e_p <= tol, (i, e_rho, e_p, tol)
     assert n_loose <= 2  # the sensitivity bound is for the rare ill-conditioned instance
