@@ -79,7 +79,7 @@ __device__ __forceinline__ double block_max_sum(double a, double b, double* sh) 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(T* __restrict__ g_rho,
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(T* __restrict__ g_rho,
                                                               T* __restrict__ g_m,
                                                               T* __restrict__ g_en,
                                                               T* __restrict__ g_ei,

@@ -50,16 +50,15 @@ struct Parab {
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
-// Appendix, Step 1: limited slope delta_m q_i.
+// Appendix, Step 1: limited slope delta_m q_i.  Branch-free: min(|dq|, 2 min(|r|, |l|))
+// equals min(|dq|, 2|r|, 2|l|) exactly (doubling is exact), and r l > 0 implies dq != 0.
 template <typename T>
 __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
   const T dq = T(0.5) * (qp - qm);
   const T r = qp - q0, l = q0 - qm;
-  if (r * l > T(0)) {
-    const T m = fmin(tabs(dq), fmin(T(2) * tabs(r), T(2) * tabs(l)));
-    return dq > T(0) ? m : -m;
-  }
-  return T(0);
+  const T m = fmin(tabs(dq), T(2) * fmin(tabs(r), tabs(l)));
+  const T sm = dq > T(0) ? m : -m;
+  return r * l > T(0) ? sm : T(0);
 }
 
 // Appendix, Step 1: 4th-order face value q_{i+1/2} from the cell values and limited slopes.
@@ -69,24 +68,23 @@ __device__ __forceinline__ T face_value(T q0, T q1, T d0, T d1) {
 }
 
 // Appendix, Steps 2-3: parabola of a cell from its value and its two face values.
+// Branch-free: the overshoot tests are evaluated on the unflattened faces and only
+// selected when the cell is not flattened, which gives the same values as the
+// sequential form (flat test first, then at most one fix).
 template <typename T>
 __device__ __forceinline__ Parab<T> parabola(T q0, T L, T R) {
-  if ((L - q0) * (q0 - R) <= T(0)) {
-    L = q0;
-    R = q0;
-  } else {
-    const T D = R - L;
-    const T S = T(6) * (q0 - T(0.5) * (L + R));
-    if (D * S > D * D)
-      L = T(3) * q0 - T(2) * R;
-    else if (D * S < -(D * D))
-      R = T(3) * q0 - T(2) * L;
-  }
+  const bool flat = (L - q0) * (q0 - R) <= T(0);
+  const T D = R - L;
+  const T S = T(6) * (q0 - T(0.5) * (L + R));
+  const bool fixL = D * S > D * D;
+  const bool fixR = !fixL && D * S < -(D * D);
+  const T Ln = flat ? q0 : (fixL ? T(3) * q0 - T(2) * R : L);
+  const T Rn = flat ? q0 : (fixR ? T(3) * q0 - T(2) * L : R);
   Parab<T> p;
-  p.L = L;
-  p.R = R;
-  p.D = R - L;
-  p.S = T(6) * (q0 - T(0.5) * (L + R));
+  p.L = Ln;
+  p.R = Rn;
+  p.D = Rn - Ln;
+  p.S = T(6) * (q0 - T(0.5) * (Ln + Rn));
   return p;
 }
 
@@ -112,6 +110,21 @@ __device__ __forceinline__ void face_constants(T rl, T rr, T pl, T pr, T gamma, 
   const T S = sl + sr;
   lam = sqrt(gamma * B / A);
   Z = sqrt(gamma * A * B / (S * S));
+}
+
+// Upwind state of eq. fluxonlagrangestage: the left cell's mean over its right fraction y
+// when the face velocity is >= 0, else the right cell's mean over its left fraction y.
+// The selected operands go through one evaluation (same operations as avg_right /
+// avg_left).
+template <typename T>
+__device__ __forceinline__ T upwind_state(bool from_left, T R_l, T D_l, T S_l, T L_r, T D_r,
+                                          T S_r, T y) {
+  const T D = from_left ? D_l : D_r;
+  const T S = from_left ? S_l : S_r;
+  const T t = S * (T(1) - Prec<T>::two_thirds(y));
+  const T u = from_left ? D - t : D + t;
+  const T w = T(0.5) * y * u;
+  return from_left ? R_l - w : L_r + w;
 }
 
 // eqs. lowriemannvelocity / lowriemannpressure from the four characteristic averages.

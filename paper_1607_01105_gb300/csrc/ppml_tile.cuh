@@ -212,59 +212,81 @@ __device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, co
   return (i + 1) + 18 * (j + 1) + 324 * (k + 1);
 }
 
-// One line of the Lagrangian stage for any axis.  Field values: core[cb + p cs] for
-// p in [0, 16), halo positions at hb + h SLP.  Face velocities vh[vb + c TN].
-// mode 0: acc = div; 1: acc += div; 2: finish (out = core - (acc + div)), written to
-// dst[gb + c gs] for c < nvalid.  have_acc: acc holds an x/y part (mode 2 only).
-template <typename T>
-__device__ __forceinline__ void lag_line(const T* fld, int cb, int cs, int hb, const T* vh,
-                                         int vb, T th, double tau, double h, int mode,
-                                         bool have_acc, T* acc, T* __restrict__ dst,
-                                         long long gb, long long gs, int nvalid) {
-  auto q = [&](int p) -> T {
-    if (p < 0) return fld[hb + (p + 3) * SLP];
-    if (p >= TB) return fld[hb + (p - TB + 3) * SLP];
-    return fld[cb + p * cs];
-  };
-  T qa = q(-3), qb = q(-2);
-  T da = T(0), fa = T(0);
-  T PR = T(0), PD = T(0), PS = T(0), Fp = T(0);
-#pragma unroll
-  for (int p = -1; p <= TB + 2; p++) {
-    const T qn = q(p);
-    const T dn = limited_slope(qa, qb, qn);
-    T fn = T(0);
-    if (p >= 0) fn = face_value(qa, qb, da, dn);
-    if (p >= 1) {
-      const Parab<T> P = parabola(qa, fa, fn);  // cell p-2
-      if (p >= 2) {
-        const T v = vh[vb + (p - 2) * TN];  // face between cells p-3 and p-2
-        const T y = Prec<T>::courant(tabs(v), tau, h, th);
-        const T F = v >= T(0) ? v * avg_right(PR, PD, PS, y) : v * avg_left(P.L, P.D, P.S, y);
-        if (p >= 3) {
-          const int c = p - 3;
-          const T d = th * (F - Fp);
-          const int o = cb + c * cs;
-          if (mode == 0) {
-            acc[o] = d;
-          } else if (mode == 1) {
-            acc[o] = acc[o] + d;
-          } else if (c < nvalid) {
-            const T dt = have_acc ? acc[o] + d : d;
-            dst[gb + gs * c] = fld[o] - dt;
-          }
-        }
-        Fp = F;
-      }
-      PR = P.R;
-      PD = P.D;
-      PS = P.S;
+// One line of the Lagrangian stage for any axis.  Field values: core[p cs] for p in
+// [0, 16), halo[h SLP] for the positions -3..-1 (h = 0..2) and 16..18 (h = 3..5).  Face
+// velocities vh[c TN], c = 0..16 (face between cells c-1 and c).  MODE 0: acc = div;
+// 1: acc += div; 2: dst[c gs] = core - (acc + div) for c < nvalid (acc only if have_acc).
+// The pipeline forms, when position p arrives, the slope at p-1, the face at p-3/2, the
+// parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
+// peeled and the steady state is a rolled loop.
+template <typename T, int MODE>
+__device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, const T* vh, T th,
+                                         double tau, double h, T* acc, bool have_acc,
+                                         T* __restrict__ dst, long long gs, int nvalid) {
+  T qa = halo[0], qb = halo[SLP];  // q(p-2), q(p-1)
+  T qn = halo[2 * SLP];            // p = -1
+  T da = limited_slope(qa, qb, qn);
+  qa = qb;
+  qb = qn;
+  qn = core[0];  // p = 0
+  T dn = limited_slope(qa, qb, qn);
+  T fa = face_value(qa, qb, da, dn);
+  qa = qb;
+  qb = qn;
+  da = dn;
+  qn = core[cs];  // p = 1
+  dn = limited_slope(qa, qb, qn);
+  T fn = face_value(qa, qb, da, dn);
+  Parab<T> P = parabola(qa, fa, fn);  // cell -1
+  T PR = P.R, PD = P.D, PS = P.S;
+  qa = qb;
+  qb = qn;
+  da = dn;
+  fa = fn;
+  qn = core[2 * cs];  // p = 2
+  dn = limited_slope(qa, qb, qn);
+  fn = face_value(qa, qb, da, dn);
+  P = parabola(qa, fa, fn);  // cell 0
+  T v = vh[0];
+  T y = Prec<T>::courant(tabs(v), tau, h, th);
+  T Fp = v * upwind_state(v >= T(0), PR, PD, PS, P.L, P.D, P.S, y);
+  PR = P.R;
+  PD = P.D;
+  PS = P.S;
+  qa = qb;
+  qb = qn;
+  da = dn;
+  fa = fn;
+  // steady state: p = 3..18 emits cell c = p-3
+  auto step = [&](T qnew, int c) {
+    const T dnn = limited_slope(qa, qb, qnew);
+    const T fnn = face_value(qa, qb, da, dnn);
+    const Parab<T> Pn = parabola(qa, fa, fnn);  // cell c+1
+    const T vv = vh[(c + 1) * TN];              // face between cells c and c+1
+    const T yy = Prec<T>::courant(tabs(vv), tau, h, th);
+    const T F = vv * upwind_state(vv >= T(0), PR, PD, PS, Pn.L, Pn.D, Pn.S, yy);
+    const T d = th * (F - Fp);
+    const int o = c * cs;
+    if (MODE == 0) {
+      acc[o] = d;
+    } else if (MODE == 1) {
+      acc[o] = acc[o] + d;
+    } else if (c < nvalid) {
+      dst[gs * c] = core[o] - (have_acc ? acc[o] + d : d);
     }
+    Fp = F;
+    PR = Pn.R;
+    PD = Pn.D;
+    PS = Pn.S;
     qa = qb;
-    qb = qn;
-    da = dn;
-    fa = fn;
-  }
+    qb = qnew;
+    da = dnn;
+    fa = fnn;
+  };
+#pragma unroll 1
+  for (int c = 0; c < TB - 3; c++) step(core[(c + 3) * cs], c);
+#pragma unroll 1
+  for (int c = TB - 3; c < TB; c++) step(halo[(c - TB + 6) * SLP], c);
 }
 
 template <typename T, int MINB>
@@ -359,11 +381,19 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       if (!act[ax]) continue;
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
+      const int cb = acc_at(li, lj, lk);
       const int cs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
-      const int m = ax == 2 ? 2 : mode;
-      lag_line<T>(S.fld, acc_at(li, lj, lk), cs, halo_at(ax, 0, tid), &S.vh[0][0][0],
-                  ax * (TB + 1) * TN + tid, th[ax], tau, A.h[ax], m, mode == 1, S.acc,
-                  A.out[f], zline0, g.nxy, nvalid_z);
+      const T* halo = &S.fld[halo_at(ax, 0, tid)];
+      const T* vhl = &S.vh[ax][0][tid];
+      if (ax == 2)
+        lag_line<T, 2>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb], mode == 1,
+                       A.out[f] + zline0, g.nxy, nvalid_z);
+      else if (mode == 0)
+        lag_line<T, 0>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb], false,
+                       nullptr, 0, 0);
+      else
+        lag_line<T, 1>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb], false,
+                       nullptr, 0, 0);
       mode = 1;
       if (ax < 2) __syncthreads();
     }
