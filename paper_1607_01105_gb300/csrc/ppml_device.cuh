@@ -56,6 +56,9 @@ template <typename T>
 __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
   const T dq = T(0.5) * (qp - qm);
   const T r = qp - q0, l = q0 - qm;
+  if (sizeof(T) == 8) {  // FP64: evaluate only what is used (same values)
+    if (!(r * l > T(0))) return T(0);
+  }
   const T m = fmin(tabs(dq), T(2) * fmin(tabs(r), tabs(l)));
   const T sm = dq > T(0) ? m : -m;
   return r * l > T(0) ? sm : T(0);
@@ -74,6 +77,14 @@ __device__ __forceinline__ T face_value(T q0, T q1, T d0, T d1) {
 template <typename T>
 __device__ __forceinline__ Parab<T> parabola(T q0, T L, T R) {
   const bool flat = (L - q0) * (q0 - R) <= T(0);
+  if (sizeof(T) == 8 && flat) {  // FP64: skip the overshoot tests of a flattened cell
+    Parab<T> p;
+    p.L = q0;
+    p.R = q0;
+    p.D = q0 - q0;
+    p.S = T(6) * (q0 - T(0.5) * (q0 + q0));
+    return p;
+  }
   const T D = R - L;
   const T S = T(6) * (q0 - T(0.5) * (L + R));
   const bool fixL = D * S > D * D;
@@ -233,20 +244,22 @@ __device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac)
 
 // Boundary handling by index mapping: interior coordinate read for coordinate c of an
 // axis with n cells (outflow: clamp; periodic: wrap; reflecting: mirror, flip = 1).
+// Coordinates further than n outside the domain (only read for cells that produce no
+// output) are clamped into range.
 __device__ __forceinline__ int bc_map(int c, int n, int lo, int hi, int& flip) {
   flip = 0;
-  if (c >= 0 && c < n) return c;
+  if ((unsigned)c < (unsigned)n) return c;
   const int bc = c < 0 ? lo : hi;
+  int r;
   if (bc == 1) {
-    int r = c % n;
-    return r < 0 ? r + n : r;
-  }
-  if (bc == 2) {
+    r = c < 0 ? c + n : c - n;
+  } else if (bc == 2) {
     flip = 1;
-    int r = c < 0 ? -1 - c : 2 * n - 1 - c;
-    return r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
+    r = c < 0 ? -1 - c : 2 * n - 1 - c;
+  } else {
+    r = c;
   }
-  return c < 0 ? 0 : n - 1;
+  return min(max(r, 0), n - 1);
 }
 
 struct GridGeom {
@@ -255,24 +268,30 @@ struct GridGeom {
   long long nxy, ncell;
 };
 
-// Linear index of possibly out-of-domain cell (i, j, k) after boundary mapping; fl[a] is
-// set when axis a was mirrored (the a-momentum changes sign there).
-__device__ __forceinline__ long long map_cell(int i, int j, int k, const GridGeom& g, int fl[3]) {
-  const int ii = bc_map(i, g.n[0], g.bc[0], g.bc[1], fl[0]);
-  const int jj = bc_map(j, g.n[1], g.bc[2], g.bc[3], fl[1]);
-  const int kk = bc_map(k, g.n[2], g.bc[4], g.bc[5], fl[2]);
+// Linear index of possibly out-of-domain cell (i, j, k) after boundary mapping; bit a of
+// flips is set when axis a was mirrored (the a-momentum changes sign there).
+__device__ __forceinline__ long long map_cell(int i, int j, int k, const GridGeom& g, int& flips) {
+  int f0, f1, f2;
+  const int ii = bc_map(i, g.n[0], g.bc[0], g.bc[1], f0);
+  const int jj = bc_map(j, g.n[1], g.bc[2], g.bc[3], f1);
+  const int kk = bc_map(k, g.n[2], g.bc[4], g.bc[5], f2);
+  flips = f0 | (f1 << 1) | (f2 << 2);
   return (long long)ii + (long long)g.n[0] * jj + g.nxy * kk;
 }
 
-// Value of field `f` (0..5; -1 for a scalar without sign flips) at possibly out-of-domain
-// cell (i, j, k), with the momentum component normal to a reflecting wall negated.
+// Sign of field f (0..5; -1 for a scalar) at a cell reached through the mirrors in flips.
+__device__ __forceinline__ bool field_flipped(int f, int flips) {
+  return f >= 1 && f <= 3 && ((flips >> (f - 1)) & 1);
+}
+
+// Value of field `f` at possibly out-of-domain cell (i, j, k), with the momentum component
+// normal to a reflecting wall negated.
 template <typename T>
 __device__ __forceinline__ T load_bc(const T* __restrict__ q, int f, int i, int j, int k,
                                      const GridGeom& g) {
-  int fl[3];
+  int fl;
   T v = __ldg(q + map_cell(i, j, k, g, fl));
-  if ((f == 1 && fl[0]) || (f == 2 && fl[1]) || (f == 3 && fl[2])) v = -v;
-  return v;
+  return field_flipped(f, fl) ? -v : v;
 }
 
 }  // namespace ppml

@@ -51,23 +51,22 @@ __device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, int tiles_x, in
   return t;
 }
 
-// Linear index of tile-relative cell (i, j, k) and the reflection flags of its mapping.
+// Linear index of tile-relative cell (i, j, k) and the mirror flags of its mapping.
 __device__ __forceinline__ long long cell_index(const GridGeom& g, const TileGeom& t, int i, int j,
-                                                int k, int fl[3]) {
+                                                int k, int& flips) {
   if (t.fast) {
-    fl[0] = fl[1] = fl[2] = 0;
+    flips = 0;
     return (long long)(t.i0 + i) + (long long)g.n[0] * (t.j0 + j) + g.nxy * (t.k0 + k);
   }
-  return map_cell(t.i0 + i, t.j0 + j, t.k0 + k, g, fl);
+  return map_cell(t.i0 + i, t.j0 + j, t.k0 + k, g, flips);
 }
 
 template <typename T>
 __device__ __forceinline__ T load_field(const T* __restrict__ q, int f, const GridGeom& g,
                                         const TileGeom& t, int i, int j, int k) {
-  int fl[3];
-  T v = q[cell_index(g, t, i, j, k, fl)];
-  if ((f == 1 && fl[0]) || (f == 2 && fl[1]) || (f == 3 && fl[2])) v = -v;
-  return v;
+  int fl;
+  const T v = q[cell_index(g, t, i, j, k, fl)];
+  return field_flipped(f, fl) ? -v : v;
 }
 
 __device__ __forceinline__ bool in_domain(const GridGeom& g, const TileGeom& t, int i, int j,
@@ -308,10 +307,10 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
     if (!act[ax]) continue;
     for (int it = tid; it < 18 * 18 * 18; it += TN) {  // v_ax = m_ax / rho over [-1, 16]^3
       const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
-      int fl[3];
+      int fl;
       const long long c = cell_index(g, tg, i, j, k, fl);
       T m = A.u[1 + ax][c];
-      if (fl[ax]) m = -m;
+      if ((fl >> ax) & 1) m = -m;
       S.fld[tbox_at(i, j, k)] = m / A.u[0][c];
     }
     __syncthreads();
@@ -330,7 +329,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
                         S.fld[o - s_b - s_c];
       const T edges = S.fld[o + s_b] + S.fld[o - s_b] + S.fld[o + s_c] + S.fld[o - s_c];
       const T vt = corners / T(16) + edges / T(8) + S.fld[o] / T(4);
-      int i, j, k, fl[3];
+      int i, j, k, fl;
       line_cell(ax, p, a, b, i, j, k);
       const T sq = sqrt(A.u[0][cell_index(g, tg, i, j, k, fl)]);
       if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
@@ -350,7 +349,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
     const T* __restrict__ src = A.u[f];
     for (int it = tid; it < TB * TB * TB; it += TN) {  // core
       const int i = it % TB, j = (it / TB) % TB, k = it / TN;
-      int fl[3];
+      int fl;
       const long long c = cell_index(g, tg, i, j, k, fl);
       T* d = &S.fld[acc_at(i, j, k)];
       if (async_ok)
@@ -365,7 +364,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const int p = h < 3 ? h - 3 : TB + h - 3;
       int i, j, k;
       line_cell(ax, p, line % TB, line / TB, i, j, k);
-      int fl[3];
+      int fl;
       const long long c = cell_index(g, tg, i, j, k, fl);
       T* d = &S.fld[halo_at(ax, h, line)];
       if (async_ok)
@@ -472,7 +471,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       }
       int i, j, k;
       line_cell(ax, p, s % TB, s / TB, i, j, k);
-      int fl[3];
+      int fl;
       const long long c = cell_index(g, tg, i, j, k, fl);
       const int o = slab_at(p, s % TB, s / TB);
       if (async_ok) {
@@ -481,7 +480,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         cp_async_elem(&S.p[o], A.u[5] + c);
       } else {
         T m = A.u[1 + ax][c];
-        if (fl[ax]) m = -m;
+        if ((fl >> ax) & 1) m = -m;
         S.r[o] = A.u[0][c];
         S.m[o] = m;
         S.p[o] = A.u[5][c];
