@@ -141,6 +141,30 @@ int ppml_profile(ppml_grid* g, int enable);
  * ms[2] finalize) and the number of profiled steps.  Synchronizes the device. */
 int ppml_kernel_times(ppml_grid* g, double ms[3], long long* steps);
 
+/* ------------------------------------------------------------ step without allocation
+ * The paper has no counterpart to this call: it exists for callers that cannot call
+ * cudaMalloc -- code running while another part of the process captures a CUDA graph
+ * (allocation is not permitted then), plugins whose host application owns the device
+ * memory budget, real-time loops that must not allocate.  It performs the same step as
+ * ppml_step (same kernels) without a handle: U*, the reduction partials and the step
+ * scalars live in a fixed device buffer inside libppml.so sized for grids of at most
+ * PPML_NOALLOC_MAX_CELLS cells (about 12 MB, held on every GPU that loads the library
+ * until the process exits).  Nothing is allocated by the call (no cudaMalloc/cudaFree).
+ *   d         the problem statement (as for ppml_init_grid); nx*ny*nz above the limit
+ *             returns PPML_E_INVAL
+ *   u_in      input state, not modified; u_out output state (no aliasing)
+ *   dt        step size, > 0 (there is no device-resident step here)
+ *   rho_mean  mean initial density, > 0 (reference of the vacuum threshold)
+ *   out       NULL, or nine doubles receiving the CFL step of u_out, max|v|, max c and the
+ *             six FP64 sums of u_out; non-NULL synchronizes the stream
+ * The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
+ * and sets the kernels' shared-memory limits; make it before any stream capture.  Every
+ * call shares the one buffer, which keeps the last call's contents: calls that overlap on
+ * the GPU (unordered streams or host threads) race on it. */
+#define PPML_NOALLOC_MAX_CELLS 262144
+int ppml_step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in, ppml_state* u_out,
+                      double dt, double rho_mean, double out[9], void* stream);
+
 /* ---------------------------------------------------------------- batched 1D problems
  * Many independent 1D problems of uneven lengths (outflow boundaries, gamma shared),
  * advanced by one persistent launch per call.  Each instance keeps its own time, CFL

@@ -90,6 +90,15 @@ __global__ void __launch_bounds__(kFinThreads)
 
 }  // namespace
 
+namespace ppml {
+int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
+                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st) {
+  finalize_kernel<<<1, kFinThreads, 0, st>>>(P, nblk, S, cfl, hmin, vol, t_end, mode, dt_dev,
+                                             dt_host);
+  return ppml_check_launch("finalize_kernel");
+}
+}  // namespace ppml
+
 struct ppml_grid {
   ppml_grid_desc d;
   GridGeom geom;
@@ -109,9 +118,7 @@ struct ppml_grid {
   long long prof_steps;
 };
 
-namespace {
-
-int validate_desc(const ppml_grid_desc* d) {
+int ppml_validate_desc(const ppml_grid_desc* d) {
   if (!d) return ppml_fail(PPML_E_INVAL, "desc is NULL");
   const int n[3] = {d->nx, d->ny, d->nz};
   for (int a = 0; a < 3; a++) {
@@ -138,7 +145,7 @@ int validate_desc(const ppml_grid_desc* d) {
   return PPML_OK;
 }
 
-int validate_state(const ppml_state* u, const char* what) {
+int ppml_validate_state(const ppml_state* u, const char* what) {
   if (!u) return ppml_fail(PPML_E_INVAL, "%s is NULL", what);
   for (int f = 0; f < 6; f++) {
     if (!u->f[f]) return ppml_fail(PPML_E_INVAL, "%s field %d is NULL", what, f);
@@ -147,6 +154,8 @@ int validate_state(const ppml_state* u, const char* what) {
   }
   return PPML_OK;
 }
+
+namespace {
 
 template <typename T>
 MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev) {
@@ -172,9 +181,8 @@ int run_diag(ppml_grid* g, const ppml_state* u, cudaStream_t st) {
   for (int f = 0; f < 6; f++) A.u[f] = (const T*)u->f[f];
   int rc = launch_diag<T>(A, g->nblk_diag, st);
   if (rc) return rc;
-  finalize_kernel<<<1, kFinThreads, 0, st>>>(g->partials, g->nblk_diag, g->dev, g->d.cfl,
-                                             g->hmin, g->vol, g->d.t_end, 0, nullptr, 0.0);
-  return ppml_check_launch("finalize_kernel");
+  return launch_finalize(g->partials, g->nblk_diag, g->dev, g->d.cfl, g->hmin, g->vol,
+                         g->d.t_end, 0, nullptr, 0.0, st);
 }
 
 template <typename T>
@@ -230,9 +238,8 @@ int run_step(ppml_grid* g, const ppml_state* uin, ppml_state* uout, const T* phi
   rc = launch_lagrangian<T>(L, g->nblk_march, st);
   if (rc) return rc;
   if (ev) cudaEventRecord(ev[2], st);
-  finalize_kernel<<<1, kFinThreads, 0, st>>>(g->partials, g->nblk_march, g->dev, g->d.cfl,
-                                             g->hmin, g->vol, g->d.t_end, 1, dt_dev, dt_host);
-  rc = ppml_check_launch("finalize_kernel");
+  rc = launch_finalize(g->partials, g->nblk_march, g->dev, g->d.cfl, g->hmin, g->vol,
+                       g->d.t_end, 1, dt_dev, dt_host, st);
   if (ev) cudaEventRecord(ev[3], st);
   return rc;
 }
@@ -244,9 +251,9 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
   ppml_clear_error();
   if (!out) return ppml_fail(PPML_E_INVAL, "out is NULL");
   *out = nullptr;
-  int rc = validate_desc(d);
+  int rc = ppml_validate_desc(d);
   if (rc) return rc;
-  rc = validate_state(u0, "u0");
+  rc = ppml_validate_state(u0, "u0");
   if (rc) return rc;
   ppml_grid* g = new (std::nothrow) ppml_grid();
   if (!g) return ppml_fail(PPML_E_NOMEM, "host allocation failed");
@@ -326,7 +333,7 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
 extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, void* stream) {
   ppml_clear_error();
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
-  int rc = validate_state(u, "u");
+  int rc = ppml_validate_state(u, "u");
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   rc = g->d.dtype == PPML_F64 ? run_diag<double>(g, u, st) : run_diag<float>(g, u, st);
@@ -344,9 +351,9 @@ extern "C" int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out
                          void* stream) {
   ppml_clear_error();
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
-  int rc = validate_state(u_in, "u_in");
+  int rc = ppml_validate_state(u_in, "u_in");
   if (rc) return rc;
-  rc = validate_state(u_out, "u_out");
+  rc = ppml_validate_state(u_out, "u_out");
   if (rc) return rc;
   for (int f = 0; f < 6; f++)
     for (int q = 0; q < 6; q++)
@@ -363,9 +370,9 @@ extern "C" int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_st
                                    double dt, void* stream) {
   ppml_clear_error();
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
-  int rc = validate_state(u_in, "u_in");
+  int rc = ppml_validate_state(u_in, "u_in");
   if (rc) return rc;
-  rc = validate_state(u_star, "u_star");
+  rc = ppml_validate_state(u_star, "u_star");
   if (rc) return rc;
   if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
   const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
@@ -379,7 +386,7 @@ extern "C" int ppml_conserved_sums(ppml_grid* g, const ppml_state* u, double out
                                    void* stream) {
   ppml_clear_error();
   if (!g || !out) return ppml_fail(PPML_E_INVAL, "grid or out is NULL");
-  int rc = validate_state(u, "u");
+  int rc = ppml_validate_state(u, "u");
   if (rc) return rc;
   // Sums go through the same partial/finalize path; the handle's scalars are restored.
   DevScalars keep, hs;

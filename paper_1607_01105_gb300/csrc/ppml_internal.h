@@ -2,9 +2,15 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/ppml.h"
+
 // Record a formatted message for ppml_last_error() on this thread and return `code`.
 int ppml_fail(int code, const char* fmt, ...);
 // Clear this thread's message (every public entry point starts with it).
 void ppml_clear_error();
 // Check cudaGetLastError() after a launch; returns PPML_OK or PPML_E_CUDA.
 int ppml_check_launch(const char* what);
+
+// Argument checks shared by the entry points (defined in ppml_grid.cu).
+int ppml_validate_desc(const ppml_grid_desc* d);
+int ppml_validate_state(const ppml_state* u, const char* what);

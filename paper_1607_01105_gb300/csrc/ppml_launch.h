@@ -22,6 +22,10 @@ template <typename T>
 int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
                  double cfl, int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st);
 
+// Deterministic reduction of per-CTA partials into the step scalars (ppml_grid.cu).
+int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
+                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st);
+
 // explicit specializations live in ppml_kern_f32.cu / ppml_kern_f64.cu
 #define PPML_DECLARE_LAUNCHERS(R)                                                            \
   template <>                                                                                \

@@ -26,7 +26,8 @@ FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
 EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppml_eulerian_stage",
             "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
-            "ppml_profile", "ppml_kernel_times")
+            "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc")
+NOALLOC_MAX_CELLS = 262144
 
 
 class GridDesc(ctypes.Structure):
@@ -65,6 +66,8 @@ _lib.ppml_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.
 _lib.ppml_batch_free.argtypes = [_vp]
 _lib.ppml_last_error.restype = ctypes.c_char_p
 _lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
+                                   ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 
 
@@ -189,6 +192,35 @@ class Grid:
         n = ctypes.c_longlong()
         _check(_lib.ppml_kernel_times(self._h, ms, ctypes.byref(n)))
         return list(ms), n.value
+
+
+def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1e-5, t_end=0.0):
+    d = GridDesc()
+    d.nx, d.ny, d.nz = (int(x) for x in n)
+    for a in range(3):
+        d.h[a] = float(h[a])
+    d.gamma, d.cfl = float(gamma), float(cfl)
+    for q in range(6):
+        d.bc[q] = int(bc[q])
+    d.dtype = int(dtype)
+    d.vacuum_frac = float(vacuum_frac)
+    d.t_end = float(t_end)
+    return d
+
+
+def step_noalloc(desc, u_in, u_out, dt, rho_mean, stream=None, want_diag=True):
+    """ppml_step_noalloc: one step without a handle and without device allocation (for
+    callers that cannot allocate).  Returns (dt_next, vmax, cmax, sums[6]) when want_diag."""
+    cells = desc.nx * desc.ny * desc.nz
+    tdt = torch_dtype(desc.dtype)
+    a = _state(u_in, tdt, cells)
+    b = _state(u_out, tdt, cells)
+    out = (ctypes.c_double * 9)()
+    _check(_lib.ppml_step_noalloc(ctypes.byref(desc), ctypes.byref(a), ctypes.byref(b), float(dt),
+                                  float(rho_mean), out if want_diag else None, _stream(stream)))
+    if not want_diag:
+        return None
+    return out[0], out[1], out[2], list(out[3:9])
 
 
 class Batch:
