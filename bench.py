@@ -31,6 +31,18 @@ N_CELLS_SIDE = 256
 # Lagrangian reads 6, writes 6.  FP64 doubles them.
 BYTES_EUL = {4: 44, 8: 88}
 BYTES_LAG = {4: 48, 8: 96}
+# algorithmic FP32 operations per cell (add, mul, fma, min, compare, select, sqrt and
+# divide each counted once) of the Lagrangian stage: 18 (field, axis) line updates of
+# 62 (slope 12, face 4, parabola 26, upwind average 17, update 3), the velocity template
+# and face velocities 57, energy correction 30, CFL terms 12, compensated sums 42.
+OPS_LAG = 18 * 62 + 57 + 30 + 12 + 42
+# Eulerian stage: per axis v and p parabolas 84, face constants 15, four averages 32,
+# face solution 9, updates 8, v = m / rho 1; plus 6 for rho E and rho eps.
+OPS_EUL = 3 * (84 + 15 + 32 + 9 + 8 + 1) + 6
+# DRAM bytes per Lagrangian launch measured by ncu (dram__bytes_read + write) on the
+# 160^3 point blast, per cell (scaled to the workload's cells); see profiles/.
+NCU_LAG_DRAM_BYTES_PER_CELL = (102.296576e6 + 63.048960e6) / 160 ** 3
+SMS, FP32_LANES = 152, 128
 
 
 def load_peaks():
@@ -191,6 +203,27 @@ def main():
         return float(t.item())
 
     results = {}
+    # batched uneven 1D Riemann problems (512 instances, 128..4096 cells): one persistent
+    # launch advances every instance to its own end time
+    from oracle import exact
+    bb = inputs.batched_riemann(max_speed=exact.riemann_max_speed)
+    bst = [torch.as_tensor(x).to(dev, torch.float32) for x in bb.u]
+    batch = ppml.Batch(bb.ncells, bb.h, bb.t_end, bb.gamma, bb.cfl, ppml.PPML_F32)
+    barrier()
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    batch.step(bst, 1 << 30)
+    b1.record(stream)
+    barrier()
+    bms = b0.elapsed_time(b1)
+    bt_t, bt_steps = batch.status()
+    batch_updates = float(np.dot(bb.ncells.astype(np.float64), np.asarray(bt_steps, dtype=np.float64)))
+    results["batch"] = {"ms": max_over_ranks(bms), "updates": batch_updates,
+                        "instances": int(bb.ncells.size), "cells": int(bb.cells),
+                        "done": int(sum(1 for t, te in zip(bt_t, bb.t_end) if t >= te))}
+    batch.close()
+    del bst
     for dtype, name in ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64")):
         elt = 4 if dtype == ppml.PPML_F32 else 8
         u = ppml.to_device(pb.u, dtype)
@@ -250,11 +283,12 @@ def main():
         value = world * cells * r32["steps"] / (r32["ms"] * 1e-3) / 1e6
         v64 = world * cells * r64["steps"] / (r64["ms"] * 1e-3) / 1e6
         keul, klag, kfin = r32["kernel_ms"]
-        dom = "lagrangian" if klag >= keul else "eulerian"
-        kname = {"lagrangian": "lagrangian stage kernel", "eulerian": "eulerian stage kernel"}[dom]
-        kms = max(klag, keul)
-        algo_bytes = (BYTES_LAG if dom == "lagrangian" else BYTES_EUL)[4] * cells
-        achieved = algo_bytes / (kms * 1e-3) / 1e9
+        clk = r32["clocks"].get("sm_max_mhz") or 2070.0
+        alu_peak = SMS * FP32_LANES * clk * 1e6 / 1e12  # FP32 lane operations, Top/s
+        lag_ops = OPS_LAG * cells / (klag * 1e-3) / 1e12
+        eul_ops = OPS_EUL * cells / (keul * 1e-3) / 1e12
+        lag_gbs = BYTES_LAG[4] * cells / (klag * 1e-3) / 1e9
+        eul_gbs = BYTES_EUL[4] * cells / (keul * 1e-3) / 1e9
         step_bytes = (BYTES_EUL[4] + BYTES_LAG[4]) * cells
         e2e = results["e2e"]
         e2e_val = world * cells * e2e["steps"] / (e2e["ms"] * 1e-3) / 1e6
@@ -269,14 +303,32 @@ def main():
                        "global_batch": 1, "seq_len": 0,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "no flush: state 403 MB x 2 + U* 336 MB > 129 MB L2"},
-            "roofline": {"bound": "hbm", "kernel": kname + " (float)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                         "algorithmic_bytes_per_cell": (BYTES_LAG if dom == "lagrangian" else BYTES_EUL)[4],
+            "roofline": {"bound": "alu", "kernel": "lagrangian_tile<float>",
+                         "achieved": lag_ops, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": lag_ops / alu_peak,
+                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clk:.0f} MHz, "
+                                       "one operation per lane per clock (FMA counted once)",
+                         "algorithmic_ops_per_cell": OPS_LAG,
+                         "traffic": NCU_LAG_DRAM_BYTES_PER_CELL * cells,
+                         "traffic_note": "ncu dram bytes of one launch on the 160^3 point blast, "
+                                         "scaled by cells",
                          "kernel_ms": {"eulerian": keul, "lagrangian": klag, "finalize": kfin},
-                         "step_hbm_frac": step_bytes / (r32["ms"] / r32["steps"] * 1e-3) / 1e9 / peak},
+                         "eulerian": {"achieved": eul_ops, "frac": eul_ops / alu_peak,
+                                      "algorithmic_ops_per_cell": OPS_EUL},
+                         "hbm": {"peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                                 "lagrangian_achieved": lag_gbs, "lagrangian_frac": lag_gbs / peak,
+                                 "eulerian_achieved": eul_gbs, "eulerian_frac": eul_gbs / peak,
+                                 "algorithmic_bytes_per_cell": BYTES_EUL[4] + BYTES_LAG[4],
+                                 "step_frac": step_bytes / (r32["ms"] / r32["steps"] * 1e-3) / 1e9 / peak}},
             "fp64": {"value": v64, "unit": "Mcell-updates/s", "ms_per_step": r64["ms"] / r64["steps"],
                      "steps": r64["steps"], "kernel_ms": r64["kernel_ms"]},
+            "batch_riemann": {"value": results["batch"]["updates"] / (results["batch"]["ms"] * 1e-3) / 1e6,
+                              "unit": "Mcell-updates/s", "ms": results["batch"]["ms"],
+                              "instances": results["batch"]["instances"],
+                              "cells": results["batch"]["cells"],
+                              "finished": results["batch"]["done"], "dtype": "f32",
+                              "workload": "512 uneven 1D Riemann problems (128..4096 cells), "
+                                          "each run to its own end time in one persistent launch"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": 3 * r32["steps"],
