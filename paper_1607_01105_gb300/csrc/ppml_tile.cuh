@@ -300,19 +300,49 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
+  const bool line_ok = in_domain(g, tg, a, b, 0);
+  const int nvalid_z = line_ok ? min(TB, g.n[2] - tg.k0) : 0;
+  const long long zline0 =
+      (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
 
   // ---- face velocities of every line (eqs. veltemplate, modspaceaveragevelocitylagrange)
-#pragma unroll 1
-  for (int ax = 0; ax < 3; ax++) {
-    if (!act[ax]) continue;
-    for (int it = tid; it < 18 * 18 * 18; it += TN) {  // v_ax = m_ax / rho over [-1, 16]^3
+  // rho and m_a over [-1, 16]^3 are staged in the field + accumulator space (free until the
+  // field loop), v_a = m_a / rho is formed in place, then each line forms its face
+  // velocities.
+  T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
+  T* rbox = smem_t;         // rho, dense 18^3
+  T* mbox = smem_t + 5832;  // m_a, then v_a
+  static_assert(2 * 5832 <= LAG_FIELD + ACC, "template boxes must fit in fld + acc");
+  const bool fast_async = async_ok && tg.fast;
+  {
+    // rho once for all three axes
+    for (int it = tid; it < 18 * 18 * 18; it += TN) {
       const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
       int fl;
       const long long c = cell_index(g, tg, i, j, k, fl);
-      T m = A.u[1 + ax][c];
-      if ((fl >> ax) & 1) m = -m;
-      S.fld[tbox_at(i, j, k)] = m / A.u[0][c];
+      if (fast_async)
+        cp_async_elem(&rbox[it], A.u[0] + c);
+      else
+        rbox[it] = A.u[0][c];
     }
+  }
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ax++) {
+    if (!act[ax]) continue;
+    for (int it = tid; it < 18 * 18 * 18; it += TN) {
+      const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
+      int fl;
+      const long long c = cell_index(g, tg, i, j, k, fl);
+      if (fast_async) {
+        cp_async_elem(&mbox[it], A.u[1 + ax] + c);
+      } else {
+        const T m = A.u[1 + ax][c];
+        mbox[it] = ((fl >> ax) & 1) ? -m : m;
+      }
+    }
+    if (fast_async) cp_async_wait_all();
+    __syncthreads();
+    for (int it = tid; it < 18 * 18 * 18; it += TN) mbox[it] = mbox[it] / rbox[it];
     __syncthreads();
     // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
     const int s_ax = ax == 0 ? 1 : (ax == 1 ? 18 : 324);
@@ -325,13 +355,11 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
 #pragma unroll 2
     for (int p = -1; p <= TB; p++) {
       const int o = base + p * s_ax;
-      const T corners = S.fld[o + s_b + s_c] + S.fld[o + s_b - s_c] + S.fld[o - s_b + s_c] +
-                        S.fld[o - s_b - s_c];
-      const T edges = S.fld[o + s_b] + S.fld[o - s_b] + S.fld[o + s_c] + S.fld[o - s_c];
-      const T vt = corners / T(16) + edges / T(8) + S.fld[o] / T(4);
-      int i, j, k, fl;
-      line_cell(ax, p, a, b, i, j, k);
-      const T sq = sqrt(A.u[0][cell_index(g, tg, i, j, k, fl)]);
+      const T corners = mbox[o + s_b + s_c] + mbox[o + s_b - s_c] + mbox[o - s_b + s_c] +
+                        mbox[o - s_b - s_c];
+      const T edges = mbox[o + s_b] + mbox[o - s_b] + mbox[o + s_c] + mbox[o - s_c];
+      const T vt = corners / T(16) + edges / T(8) + mbox[o] / T(4);
+      const T sq = sqrt(rbox[o]);
       if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
       vt_prev = vt;
       sq_prev = sq;
@@ -340,37 +368,52 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   }
 
   // ---- per field: stage, sweep x, y (into acc), z (finish into the output)
-  const bool line_ok = in_domain(g, tg, a, b, 0);
-  const int nvalid_z = line_ok ? min(TB, g.n[2] - tg.k0) : 0;
-  const long long zline0 =
-      (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
 #pragma unroll 1
   for (int f = 0; f < 6; f++) {
     const T* __restrict__ src = A.u[f];
-    for (int it = tid; it < TB * TB * TB; it += TN) {  // core
-      const int i = it % TB, j = (it / TB) % TB, k = it / TN;
-      int fl;
-      const long long c = cell_index(g, tg, i, j, k, fl);
-      T* d = &S.fld[acc_at(i, j, k)];
-      if (async_ok)
-        cp_async_elem(d, src + c);
-      else
-        *d = load_field(src, f, g, tg, i, j, k);
-    }
-    for (int it = tid; it < 3 * HALO_POS * TN; it += TN) {  // halo positions, active axes
-      const int ax = it / (HALO_POS * TN), r = it % (HALO_POS * TN);
-      if (!act[ax]) continue;
-      const int h = r / TN, line = r % TN;
-      const int p = h < 3 ? h - 3 : TB + h - 3;
-      int i, j, k;
-      line_cell(ax, p, line % TB, line / TB, i, j, k);
-      int fl;
-      const long long c = cell_index(g, tg, i, j, k, fl);
-      T* d = &S.fld[halo_at(ax, h, line)];
-      if (async_ok)
-        cp_async_elem(d, src + c);
-      else
-        *d = load_field(src, f, g, tg, i, j, k);
+    if (fast_async) {
+      // interior tile: thread (a, b) copies the z column (a, b, *) of the core and the six
+      // halo positions of its x, y and z lines
+      const T* col = src + zline0;
+      T* dcore = &S.fld[acc_at(a, b, 0)];
+#pragma unroll 4
+      for (int s = 0; s < TB; s++) cp_async_elem(dcore + s * APP, col + g.nxy * s);
+      const long long nx = g.n[0];
+      const T* xl = src + (long long)tg.i0 + nx * (tg.j0 + a) + g.nxy * (tg.k0 + b);
+      const T* yl = src + (long long)(tg.i0 + a) + nx * tg.j0 + g.nxy * (tg.k0 + b);
+#pragma unroll
+      for (int h = 0; h < HALO_POS; h++) {
+        const int p = h < 3 ? h - 3 : TB + h - 3;
+        if (act[0]) cp_async_elem(&S.fld[halo_at(0, h, tid)], xl + p);
+        if (act[1]) cp_async_elem(&S.fld[halo_at(1, h, tid)], yl + nx * p);
+        if (act[2]) cp_async_elem(&S.fld[halo_at(2, h, tid)], col + g.nxy * p);
+      }
+    } else {
+      for (int it = tid; it < TB * TB * TB; it += TN) {  // core
+        const int i = it % TB, j = (it / TB) % TB, k = it / TN;
+        int fl;
+        const long long c = cell_index(g, tg, i, j, k, fl);
+        T* d = &S.fld[acc_at(i, j, k)];
+        if (async_ok)
+          cp_async_elem(d, src + c);
+        else
+          *d = load_field(src, f, g, tg, i, j, k);
+      }
+      for (int it = tid; it < 3 * HALO_POS * TN; it += TN) {  // halo positions, active axes
+        const int ax = it / (HALO_POS * TN), r = it % (HALO_POS * TN);
+        if (!act[ax]) continue;
+        const int h = r / TN, line = r % TN;
+        const int p = h < 3 ? h - 3 : TB + h - 3;
+        int i, j, k;
+        line_cell(ax, p, line % TB, line / TB, i, j, k);
+        int fl;
+        const long long c = cell_index(g, tg, i, j, k, fl);
+        T* d = &S.fld[halo_at(ax, h, line)];
+        if (async_ok)
+          cp_async_elem(d, src + c);
+        else
+          *d = load_field(src, f, g, tg, i, j, k);
+      }
     }
     if (async_ok) cp_async_wait_all();
     __syncthreads();
@@ -410,6 +453,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   sums.init();
   T vmax = T(0), cmax = T(0);
   unsigned long long nvac = 0, nbad = 0;
+#pragma unroll 2
   for (int c = 0; c < nvalid_z; c++) {
     const long long idx = zline0 + g.nxy * c;
     T u[6];
@@ -459,7 +503,24 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
     // stage rho, m_ax, rho eps along the axis: position p in [-3, 18], transverse
-    // (s % 16, s / 16)
+    // (s % 16, s / 16); on interior tiles each thread copies its own line
+    if (async_ok && tg.fast) {
+      int li, lj, lk;
+      line_cell(ax, 0, a, b, li, lj, lk);
+      const long long lb =
+          (long long)(tg.i0 + li) + (long long)g.n[0] * (tg.j0 + lj) + g.nxy * (tg.k0 + lk);
+      const long long st = ax == 0 ? 1 : (ax == 1 ? (long long)g.n[0] : g.nxy);
+      const T* rl = A.u[0] + lb;
+      const T* ml = A.u[1 + ax] + lb;
+      const T* el = A.u[5] + lb;
+#pragma unroll 2
+      for (int p = -TH; p < TB + TH; p++) {
+        const int o = slab_at(p, a, b);
+        cp_async_elem(&S.r[o], rl + st * p);
+        cp_async_elem(&S.m[o], ml + st * p);
+        cp_async_elem(&S.p[o], el + st * p);
+      }
+    } else
     for (int it = tid; it < TW * TN; it += TN) {
       int p, s;
       if (ax == 0) {  // x fastest in memory: walk p fastest
