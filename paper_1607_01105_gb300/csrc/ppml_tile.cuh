@@ -503,8 +503,9 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
     // stage rho, m_ax, rho eps along the axis: position p in [-3, 18], transverse
-    // (s % 16, s / 16); on interior tiles each thread copies its own line
-    if (async_ok && tg.fast) {
+    // (s % 16, s / 16); on interior tiles the y and z lines are copied by their owners
+    // (lanes consecutive in x), the x slab walks x fastest
+    if (async_ok && tg.fast && ax > 0) {
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
       const long long lb =
