@@ -116,6 +116,25 @@ int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, void* stream
  * u_in and u_out must not alias; u_in is not modified.  Asynchronous. */
 int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, double dt, void* stream);
 
+/* ppml_step with a gravitational potential (paper eqs. for rho v and rho E: the source
+ * terms -rho grad Phi and -rho v . grad Phi).  phi: device array of nx*ny*nz cells of the
+ * state's type, or NULL (then identical to ppml_step).  The Eulerian stage adds
+ * m -= tau rho grad Phi and rho E -= tau m . grad Phi from U^n with cell-centred central
+ * differences of Phi (boundary values of Phi: zero-gradient at outflow and reflecting
+ * faces, wrapped at periodic ones). */
+int ppml_step_phi(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const void* phi,
+                  double dt, void* stream);
+
+/* Periodic solve of the 27-point discretisation of Delta Phi = 4 pi G rho (paper Sec. "The
+ * Poisson solver", eq. stencil27point and the harmonic-space formula of its Stages 2-3):
+ * Phi = IFFT( -(2/3) pi G h^2 FFT(rho) / (1 - prod_a (1 - (2/3) sin^2(pi k_a/N_a))) ), the
+ * k = 0 mode set to zero (the potential of rho minus its mean).  The printed formula lacks
+ * the minus sign that the stencil's symbol carries.  Requires h[0] = h[1] = h[2] on active
+ * axes.  rho, phi: device arrays of nx*ny*nz cells of the grid's type (may not alias).
+ * Uses cuFFT plans and a spectrum buffer created on the first call and kept in the handle.
+ * Asynchronous. */
+int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, double G, void* stream);
+
 /* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated) into
  * u_star.  For stage-level checks; same dt convention as ppml_step; does not advance t. */
 int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star, double dt,

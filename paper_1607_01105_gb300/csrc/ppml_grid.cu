@@ -15,8 +15,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <cufft.h>
+
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/ppml.h"
 #include "ppml_internal.h"
@@ -116,6 +119,11 @@ struct ppml_grid {
   int ev_used;
   double ms[3];
   long long prof_steps;
+  // periodic Poisson solve: cuFFT plans, half spectrum and per-axis symbol tables
+  int fft_ready;
+  cufftHandle fft_fwd, fft_inv;
+  void* spec;
+  double* tables;
 };
 
 int ppml_validate_desc(const ppml_grid_desc* d) {
@@ -326,7 +334,65 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
     for (int q = 0; q < 4 * ppml_grid::kEvSlots; q++) cudaEventDestroy(g->ev[q]);
     delete[] g->ev;
   }
+  if (g->fft_ready) {
+    cufftDestroy(g->fft_fwd);
+    cufftDestroy(g->fft_inv);
+  }
+  if (g->spec) cudaFree(g->spec);
+  if (g->tables) cudaFree(g->tables);
   delete g;
+  return PPML_OK;
+}
+
+extern "C" int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, double G,
+                                     void* stream) {
+  ppml_clear_error();
+  if (!g || !rho || !phi) return ppml_fail(PPML_E_INVAL, "grid, rho or phi is NULL");
+  if (rho == phi) return ppml_fail(PPML_E_INVAL, "rho and phi alias");
+  if (!isfinite(G)) return ppml_fail(PPML_E_INVAL, "G is not finite");
+  const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+  for (int a = 1; a < 3; a++)
+    if (n[a] > 1 && fabs(g->d.h[a] - g->d.h[0]) > 1e-12 * g->d.h[0])
+      return ppml_fail(PPML_E_INVAL, "the 27-point solve needs equal cell sizes");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f64 = g->d.dtype == PPML_F64;
+  const int mx = n[0] / 2 + 1;
+  if (!g->fft_ready) {
+    const size_t cbytes = (size_t)mx * n[1] * n[2] * 2 * g->elt;
+    if (cudaMalloc(&g->spec, cbytes) != cudaSuccess ||
+        cudaMalloc(&g->tables, sizeof(double) * (size_t)(mx + n[1] + n[2])) != cudaSuccess)
+      return ppml_fail(PPML_E_NOMEM, "Poisson buffers");
+    std::vector<double> tab;
+    const int len[3] = {mx, n[1], n[2]};
+    for (int a = 0; a < 3; a++)
+      for (int k = 0; k < len[a]; k++) {
+        const double s = sin(M_PI * (double)k / (double)n[a]);
+        tab.push_back(1.0 - (2.0 / 3.0) * s * s);
+      }
+    if (cudaMemcpy(g->tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return ppml_fail(PPML_E_CUDA, "Poisson tables: %s", cudaGetErrorString(cudaGetLastError()));
+    if (cufftPlan3d(&g->fft_fwd, n[2], n[1], n[0], f64 ? CUFFT_D2Z : CUFFT_R2C) != CUFFT_SUCCESS ||
+        cufftPlan3d(&g->fft_inv, n[2], n[1], n[0], f64 ? CUFFT_Z2D : CUFFT_C2R) != CUFFT_SUCCESS)
+      return ppml_fail(PPML_E_CUDA, "cufftPlan3d failed");
+    g->fft_ready = 1;
+  }
+  if (cufftSetStream(g->fft_fwd, st) != CUFFT_SUCCESS || cufftSetStream(g->fft_inv, st) != CUFFT_SUCCESS)
+    return ppml_fail(PPML_E_CUDA, "cufftSetStream failed");
+  cufftResult r = f64 ? cufftExecD2Z(g->fft_fwd, (cufftDoubleReal*)rho, (cufftDoubleComplex*)g->spec)
+                      : cufftExecR2C(g->fft_fwd, (cufftReal*)rho, (cufftComplex*)g->spec);
+  if (r != CUFFT_SUCCESS) return ppml_fail(PPML_E_CUDA, "cuFFT forward failed (%d)", (int)r);
+  const double h = g->d.h[0];
+  const double coef = -(2.0 / 3.0) * M_PI * G * h * h / ((double)n[0] * n[1] * n[2]);
+  const double* tx = g->tables;
+  const double* ty = tx + mx;
+  const double* tz = ty + n[1];
+  int rc = f64 ? launch_poisson_symbol<double>(g->spec, tx, ty, tz, mx, n[1], n[2], coef, st)
+               : launch_poisson_symbol<float>(g->spec, tx, ty, tz, mx, n[1], n[2], coef, st);
+  if (rc) return rc;
+  r = f64 ? cufftExecZ2D(g->fft_inv, (cufftDoubleComplex*)g->spec, (cufftDoubleReal*)phi)
+          : cufftExecC2R(g->fft_inv, (cufftComplex*)g->spec, (cufftReal*)phi);
+  if (r != CUFFT_SUCCESS) return ppml_fail(PPML_E_CUDA, "cuFFT inverse failed (%d)", (int)r);
   return PPML_OK;
 }
 
@@ -347,8 +413,25 @@ extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, v
   return PPML_OK;
 }
 
+static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const void* phi,
+                       double dt, void* stream);
+
 extern "C" int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, double dt,
                          void* stream) {
+  return step_common(g, u_in, u_out, nullptr, dt, stream);
+}
+
+extern "C" int ppml_step_phi(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out,
+                             const void* phi, double dt, void* stream) {
+  if (phi && (((uintptr_t)phi) & 15u)) {
+    ppml_clear_error();
+    return ppml_fail(PPML_E_INVAL, "phi is not 16-byte aligned");
+  }
+  return step_common(g, u_in, u_out, phi, dt, stream);
+}
+
+static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const void* phi,
+                       double dt, void* stream) {
   ppml_clear_error();
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
   int rc = ppml_validate_state(u_in, "u_in");
@@ -362,8 +445,8 @@ extern "C" int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out
   const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
   cudaStream_t st = (cudaStream_t)stream;
   return g->d.dtype == PPML_F64
-             ? run_step<double>(g, u_in, u_out, nullptr, dt, dt_dev, st)
-             : run_step<float>(g, u_in, u_out, nullptr, dt, dt_dev, st);
+             ? run_step<double>(g, u_in, u_out, (const double*)phi, dt, dt_dev, st)
+             : run_step<float>(g, u_in, u_out, (const float*)phi, dt, dt_dev, st);
 }
 
 extern "C" int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star,

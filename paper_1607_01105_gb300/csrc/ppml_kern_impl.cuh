@@ -54,6 +54,39 @@ int launch_diag<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t
   return ppml_check_launch("diag_kernel");
 }
 
+namespace {
+// Multiply the half spectrum (R2C layout: kx in [0, nx/2], ky, kz) by the inverse symbol of
+// the 27-point stencil; tables hold 1 - (2/3) sin^2(pi k / N) per axis.
+template <typename T>
+__global__ void poisson_symbol_kernel(T* spec, const double* __restrict__ tx,
+                                      const double* __restrict__ ty,
+                                      const double* __restrict__ tz, int mx, int ny, int nz,
+                                      double coef) {
+  const long long n = (long long)mx * ny * nz;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(idx % mx);
+    const long long r = idx / mx;
+    const int ky = (int)(r % ny), kz = (int)(r / ny);
+    const double den = 1.0 - tz[kz] * ty[ky] * tx[kx];
+    const double f = idx == 0 ? 0.0 : coef / den;
+    spec[2 * idx] = (T)(spec[2 * idx] * f);
+    spec[2 * idx + 1] = (T)(spec[2 * idx + 1] * f);
+  }
+}
+}  // namespace
+
+template <>
+int launch_poisson_symbol<PPML_REAL>(void* spec, const double* tx, const double* ty,
+                                     const double* tz, int mx, int ny, int nz, double coef,
+                                     cudaStream_t st) {
+  const long long n = (long long)mx * ny * nz;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  poisson_symbol_kernel<PPML_REAL><<<blocks, 256, 0, st>>>((PPML_REAL*)spec, tx, ty, tz, mx, ny, nz,
+                                                           coef);
+  return ppml_check_launch("poisson_symbol_kernel");
+}
+
 template <>
 int launch_batch<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
                             InstDev* inst, const int* order, double gamma, double cfl,

@@ -19,6 +19,9 @@ int launch_lagrangian(const MarchArgs<T>& A, int nblk, cudaStream_t st);
 template <typename T>
 int launch_diag(const MarchArgs<T>& A, int nblk, cudaStream_t st);
 template <typename T>
+int launch_poisson_symbol(void* spec, const double* tx, const double* ty, const double* tz, int mx,
+                          int ny, int nz, double coef, cudaStream_t st);
+template <typename T>
 int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
                  double cfl, int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st);
 
@@ -36,6 +39,10 @@ int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, doubl
   int launch_lagrangian<R>(const MarchArgs<R>& A, int nblk, cudaStream_t st);                 \
   template <>                                                                                \
   int launch_diag<R>(const MarchArgs<R>& A, int nblk, cudaStream_t st);                       \
+  template <>                                                                                \
+  int launch_poisson_symbol<R>(void* spec, const double* tx, const double* ty,                 \
+                               const double* tz, int mx, int ny, int nz, double coef,          \
+                               cudaStream_t st);                                               \
   template <>                                                                                \
   int launch_batch<R>(R * rho, R * m, R * en, R * ei, InstDev * inst, const int* order,       \
                       double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem, \

@@ -590,14 +590,17 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     const T dvs = first ? T(0) : S.av[acc_at(a, b, c)];
     T en = A.u[4][idx] - dpvs;
     if (A.phi) {
+      GridGeom gp = g;  // Phi: zero-gradient at reflecting walls, like at outflow faces
+      for (int q = 0; q < 6; q++)
+        if (gp.bc[q] == 2) gp.bc[q] = 0;
       T m[3] = {A.out[1][idx], A.out[2][idx], A.out[3][idx]};
       const T m0[3] = {A.u[1][idx], A.u[2][idx], A.u[3][idx]};
 #pragma unroll 1
       for (int ax = 0; ax < 3; ax++) {
         if (!act[ax]) continue;
         const int di = ax == 0, dj = ax == 1, dk = ax == 2;
-        const T pp = load_bc(A.phi, -1, gi + di, gj + dj, gk + dk, g);
-        const T pm = load_bc(A.phi, -1, gi - di, gj - dj, gk - dk, g);
+        const T pp = load_bc(A.phi, -1, gi + di, gj + dj, gk + dk, gp);
+        const T pm = load_bc(A.phi, -1, gi - di, gj - dj, gk - dk, gp);
         const T grad = (pp - pm) / T(2.0 * A.h[ax]);
         m[ax] -= T(tau) * rho0 * grad;
         en -= T(tau) * m0[ax] * grad;

@@ -26,7 +26,8 @@ FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
 EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppml_eulerian_stage",
             "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
-            "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc")
+            "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
+            "ppml_poisson_periodic")
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -66,6 +67,8 @@ _lib.ppml_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.
 _lib.ppml_batch_free.argtypes = [_vp]
 _lib.ppml_last_error.restype = ctypes.c_char_p
 _lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_step_phi.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), _vp, ctypes.c_double, _vp]
+_lib.ppml_poisson_periodic.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -158,6 +161,22 @@ class Grid:
         a = _state(u_in, self.tdtype, self.cells)
         b = _state(u_out, self.tdtype, self.cells)
         _check(_lib.ppml_step(self._h, ctypes.byref(a), ctypes.byref(b), float(dt), _stream(stream)))
+
+    def step_phi(self, u_in, u_out, phi, dt=0.0, stream=None):
+        """Step with the gravitational potential phi (device tensor of the grid's dtype)."""
+        a = _state(u_in, self.tdtype, self.cells)
+        b = _state(u_out, self.tdtype, self.cells)
+        if phi is not None and (not phi.is_cuda or phi.dtype != self.tdtype or phi.numel() != self.cells):
+            raise ValueError("phi must be a CUDA tensor of the grid's dtype and size")
+        _check(_lib.ppml_step_phi(self._h, ctypes.byref(a), ctypes.byref(b),
+                                  phi.data_ptr() if phi is not None else None, float(dt), _stream(stream)))
+
+    def poisson_periodic(self, rho, phi, G=1.0, stream=None):
+        """Periodic 27-point Poisson solve of rho into phi (device tensors, grid dtype)."""
+        for t in (rho, phi):
+            if not t.is_cuda or t.dtype != self.tdtype or t.numel() != self.cells or not t.is_contiguous():
+                raise ValueError("rho and phi must be contiguous CUDA tensors of the grid's dtype and size")
+        _check(_lib.ppml_poisson_periodic(self._h, rho.data_ptr(), phi.data_ptr(), float(G), _stream(stream)))
 
     def eulerian_stage(self, u_in, u_star, dt, stream=None):
         a = _state(u_in, self.tdtype, self.cells)

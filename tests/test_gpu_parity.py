@@ -410,6 +410,90 @@ def test_config4_full_batch_sampled_instances():
             assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
 
 
+# ------------------------------------------------------------- gravity and config 5
+
+@pytest.mark.parametrize("dtype,tol", [(F64, 1e-12), (F32, 2e-5)])
+def test_poisson_periodic_matches_oracle(dtype, tol):
+    from oracle import poisson
+    rng = np.random.default_rng(5)
+    n = (40, 24, 16)
+    rho = rng.uniform(0.5, 2.0, size=(n[2], n[1], n[0]))
+    h, G = 0.03, 1.7
+    ref = poisson.solve_periodic(rho, h, G)
+    u = ppml.to_device([rho] * 6, dtype)
+    grid = ppml.Grid(n, (h, h, h), 1.4, 0.2, (1,) * 6, dtype, u0=u)
+    phi = torch.empty_like(u[0])
+    grid.poisson_periodic(u[0], phi, G)
+    got = phi.double().cpu().numpy().reshape(ref.shape)
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_outflow_3d", "rough_2d"])
+def test_gravity_step_fp64_bitwise(case):
+    """Step with a potential: the source terms of the Eulerian stage reproduce the oracle
+    bit for bit in FP64."""
+    pb = CASES[case]()
+    rng = np.random.default_rng(8)
+    phi = rng.normal(size=(pb.n[2], pb.n[1], pb.n[0]))
+    g = oracle_grid(pb)
+    dt = oracle.cfl_dt(g, pb.u)
+    ref, _ = oracle.step(g, pb.u, dt, phi=phi)
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    grid.step_phi(u, v, torch.as_tensor(phi.ravel()).cuda(), dt)
+    got = host(v, shape_of(pb))
+    assert [int(np.count_nonzero(got[f] != ref[f])) for f in range(6)] == [0] * 6
+
+
+def _disk_run_oracle(pb, steps):
+    from oracle import poisson
+    g = oracle_grid(pb)
+    u = pb.u
+    dts = []
+    for _ in range(steps):
+        phi = poisson.solve_periodic(u[0], pb.h[0]) + pb.extra["phi_halo"]
+        dts.append(oracle.cfl_dt(g, u))
+        u, dg = oracle.step(g, u, dts[-1], phi=phi)
+    return u, dts, dg
+
+
+def _disk_run_gpu(pb, dtype, dts):
+    u = ppml.to_device(pb.u, dtype)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, dtype, u)
+    halo = torch.as_tensor(pb.extra["phi_halo"].ravel()).to("cuda", ppml.torch_dtype(dtype))
+    phi = torch.empty_like(u[0])
+    for dt in dts:
+        grid.poisson_periodic(u[0], phi, 1.0)
+        phi.add_(halo)
+        grid.step_phi(u, v, phi, dt)
+        u, v = v, u
+    return host(u, shape_of(pb)), grid
+
+
+def test_config5_disk_64_fp64():
+    """Galactic disk (config 5 setup) at 64^3 in FP64: self-gravity from the periodic
+    Poisson solve plus the fixed halo potential, 12 steps against the oracle (1e-10)."""
+    pb = inputs.galactic_disk(n=64)
+    ref, dts, dg = _disk_run_oracle(pb, 12)
+    got, grid = _disk_run_gpu(pb, F64, dts)
+    compare(got, ref, TOL64)
+
+
+@pytest.mark.slow
+def test_config5_disk_512_fp32():
+    """Config 5 at full size: the 512^3 disk in FP32, two gravity steps against the FP64
+    oracle (rho and p within 1e-3), and FP64 sums of mass and energy within 1e-6."""
+    pb = inputs.galactic_disk(n=512)
+    ref, dts, dg = _disk_run_oracle(pb, 2)
+    got, grid = _disk_run_gpu(pb, F32, dts)
+    compare(got, ref, 1e-3, fields=(0, 5))
+    d = grid.diag()
+    assert d["sums"][0] == pytest.approx(dg["sums"][0], rel=1e-6)
+    assert d["sums"][4] == pytest.approx(dg["sums"][4], rel=1e-6)
+
+
 def test_cuda_graph_replay_equals_eager():
     """Steps using the device-resident dt can be captured in a CUDA graph; replaying the
     graph gives bitwise the eager result."""

@@ -458,3 +458,35 @@ def test_point_blast_radius_matches_sedov():
     r_peak = bins[np.argmax(prof)] + 0.5 * h
     R = xi0 * (1.0 * t * t / 1.0) ** 0.2
     assert abs(r_peak - R) <= 2.0 * h, (r_peak, R)
+
+
+# ------------------------------------------------------------------- Poisson (S12)
+
+def test_poisson_solution_satisfies_the_printed_stencil():
+    """The harmonic-space solve inverts eq. stencil27point: applying the printed 27-point
+    weights (-38/9, 4/9, 1/9, 1/36) to Phi gives 4 pi G h^2 (rho - mean rho) to round-off.
+    A wrong sign, a missing 2/3 or a transposed axis in the symbol fails this."""
+    from oracle import poisson
+    rng = np.random.default_rng(21)
+    rho = rng.uniform(0.5, 2.0, size=(12, 10, 16))
+    h, G = 0.05, 1.3
+    phi = poisson.solve_periodic(rho, h, G)
+    lhs = poisson.apply_stencil(phi)
+    rhs = 4.0 * math.pi * G * h * h * (rho - rho.mean())
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+    assert abs(phi.mean()) <= 1e-14 * np.max(np.abs(phi))
+
+
+def test_poisson_converges_to_the_continuous_potential():
+    """For rho = sin(2 pi x) sin(2 pi y) sin(2 pi z) the continuum potential is
+    -4 pi G rho / (3 (2 pi)^2); the discrete solution converges at second order or better."""
+    from oracle import poisson
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / n
+        c = (np.arange(n) + 0.5) * h
+        z, y, x = np.meshgrid(c, c, c, indexing="ij")
+        rho = np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y) * np.sin(2 * math.pi * z)
+        exact = -4 * math.pi * rho / (3 * (2 * math.pi) ** 2)
+        errs.append(np.max(np.abs(poisson.solve_periodic(rho, h) - exact)))
+    assert math.log2(errs[0] / errs[1]) >= 1.9
