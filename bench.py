@@ -53,6 +53,22 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """Largest value of x over all ranks (the job's time is the slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, steps, world, ms):
+    """Cell-updates per second of the whole job (all ranks' work over the slowest time), in
+    Mcell-updates/s."""
+    return world * cells_per_rank * steps / (ms * 1e-3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -195,12 +211,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_(x):
+        return max_over_ranks(x, dist, dev)
 
     results = {}
     # batched uneven 1D Riemann problems (512 instances, 128..4096 cells): one persistent
@@ -219,7 +231,7 @@ def main():
     bms = b0.elapsed_time(b1)
     bt_t, bt_steps = batch.status()
     batch_updates = float(np.dot(bb.ncells.astype(np.float64), np.asarray(bt_steps, dtype=np.float64)))
-    results["batch"] = {"ms": max_over_ranks(bms), "updates": batch_updates,
+    results["batch"] = {"ms": max_over_ranks_(bms), "updates": batch_updates,
                         "instances": int(bb.ncells.size), "cells": int(bb.cells),
                         "done": int(sum(1 for t, te in zip(bt_t, bb.t_end) if t >= te))}
     batch.close()
@@ -249,7 +261,7 @@ def main():
         kms, ksteps = grid.kernel_times()
         grid.profile(False)
         d = grid.diag(raise_nonphysical=False)
-        ms = max_over_ranks(ms)
+        ms = max_over_ranks_(ms)
         results[name] = {"ms": ms, "steps": steps, "kernel_ms": [x / ksteps for x in kms],
                          "clocks": cs.summary(), "elt": elt, "diag": d}
         # end to end through host buffers (FP32 headline only): pinned H2D of the input
@@ -270,7 +282,7 @@ def main():
                     dst.copy_(src, non_blocking=True)
             e1.record(stream)
             barrier()
-            ems = max_over_ranks(e0.elapsed_time(e1))
+            ems = max_over_ranks_(e0.elapsed_time(e1))
             results["e2e"] = {"ms": ems, "steps": e_steps,
                               "h2d": 6 * cells * elt, "d2h": 6 * cells * elt}
         grid.close()
@@ -280,8 +292,8 @@ def main():
     if rank == 0:
         peak, peak_kind = load_peaks()
         r32, r64 = results["f32"], results["f64"]
-        value = world * cells * r32["steps"] / (r32["ms"] * 1e-3) / 1e6
-        v64 = world * cells * r64["steps"] / (r64["ms"] * 1e-3) / 1e6
+        value = whole_job_rate(cells, r32["steps"], world, r32["ms"])
+        v64 = whole_job_rate(cells, r64["steps"], world, r64["ms"])
         keul, klag, kfin = r32["kernel_ms"]
         clk = r32["clocks"].get("sm_max_mhz") or 2070.0
         alu_peak = SMS * FP32_LANES * clk * 1e6 / 1e12  # FP32 lane operations, Top/s
@@ -291,7 +303,7 @@ def main():
         eul_gbs = BYTES_EUL[4] * cells / (keul * 1e-3) / 1e9
         step_bytes = (BYTES_EUL[4] + BYTES_LAG[4]) * cells
         e2e = results["e2e"]
-        e2e_val = world * cells * e2e["steps"] / (e2e["ms"] * 1e-3) / 1e6
+        e2e_val = whole_job_rate(cells, e2e["steps"], world, e2e["ms"])
         line = {
             "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
             "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"] / r32["steps"],
