@@ -56,6 +56,12 @@ typedef enum {
 
 typedef enum { PPML_BC_OUTFLOW = 0, PPML_BC_PERIODIC = 1, PPML_BC_REFLECT = 2 } ppml_bc;
 
+/* scheme variants (ppml_grid_desc.flags) */
+#define PPML_FIRST_ORDER 1u /* piecewise-constant states in both stages (Sec. 1.1, the first-order
+                               scheme the paper compares against) */
+#define PPML_VHAT_1PT 2u    /* face velocity of the Lagrangian stage from the line only, without
+                               the 9-point template (the 1-point variant of Sec. 1.3) */
+
 /* flag bits accumulated on the device (ppml_diag.flags) */
 #define PPML_FLAG_NONPHYSICAL 1u /* an output cell had rho <= 0, rho eps <= 0 or a NaN/Inf */
 #define PPML_FLAG_DT_ZERO 2u     /* the CFL step underflowed to 0 (or t_end reached) */
@@ -73,6 +79,7 @@ typedef struct {
                          initial density (paper Sec. 1.4: five orders of magnitude, 1e-5);
                          <= 0 selects 1e-5 */
   double t_end;       /* > 0: the device-side CFL step is clipped so t lands on t_end */
+  int flags;          /* PPML_FIRST_ORDER | PPML_VHAT_1PT variants; 0 = the PPML scheme */
 } ppml_grid_desc;
 
 /* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions). */

@@ -23,6 +23,7 @@ _SRC = os.path.join(_HERE, "ppml_oracle.c")
 _LIB = os.path.join(_HERE, "libppml_oracle.so")
 
 BC_OUTFLOW, BC_PERIODIC, BC_REFLECT = 0, 1, 2
+FIRST_ORDER, VHAT_1PT = 1, 2  # scheme variants (Sec. 1.1 first order; 1-point face velocity)
 FIELDS = ("rho", "mx", "my", "mz", "en", "ei")
 
 
@@ -40,7 +41,7 @@ def build(force: bool = False) -> str:
 class _Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 6), ("h", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("vacuum_frac", ctypes.c_double),
-                ("rho_mean", ctypes.c_double)]
+                ("rho_mean", ctypes.c_double), ("flags", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
@@ -92,6 +93,7 @@ class Grid:
     cfl: float = 0.2
     vacuum_frac: float = 1e-5
     rho_mean: float = 1.0
+    flags: int = 0
 
     def desc(self) -> _Desc:
         d = _Desc()
@@ -103,6 +105,7 @@ class Grid:
         d.gamma = float(self.gamma)
         d.vacuum_frac = float(self.vacuum_frac)
         d.rho_mean = float(self.rho_mean)
+        d.flags = int(self.flags)
         return d
 
 

@@ -65,7 +65,12 @@ typedef struct {
   double gamma;        /* ratio of specific heats */
   double vacuum_frac;  /* vacuum threshold relative to rho_mean */
   double rho_mean;     /* mean initial density */
+  int flags;           /* ORACLE_FIRST_ORDER: piecewise-constant states (Sec. 1.1);
+                          ORACLE_VHAT_1PT: face velocity from the line only (no 9-point
+                          template, the 1-point variant the paper compares against) */
 } oracle_desc;
+#define ORACLE_FIRST_ORDER 1
+#define ORACLE_VHAT_1PT 2
 
 typedef struct {
   double dt_cfl;       /* CFL step of the output state for the given cfl number */
@@ -188,8 +193,30 @@ static double limited_slope(double qm, double q0, double qp) {
 /* Appendix, Steps 1-3, on one line q[0..N-1] (ghost-padded).  Outputs the parabola
  * (qL, qR, dq = qR - qL, q6) of every cell c in [2, N-3]; other entries are untouched.
  * work must hold N doubles for delta_m q and N for the face values. */
+static void line_parabolas_ex(const double* q, int N, double* work, double* qL, double* qR,
+                              double* dq, double* q6, int first_order);
 static void line_parabolas(const double* q, int N, double* work, double* qL, double* qR,
                            double* dq, double* q6) {
+  line_parabolas_ex(q, N, work, qL, qR, dq, q6, 0);
+}
+
+/* First-order variant (Sec. 1.1, piecewise-constant initial data of the face problems):
+ * every cell's "parabola" is the constant cell value. */
+static void line_flat(const double* q, int N, double* qL, double* qR, double* dq, double* q6) {
+  for (int c = 2; c <= N - 3; c++) {
+    qL[c] = q[c];
+    qR[c] = q[c];
+    dq[c] = 0.0;
+    q6[c] = 0.0;
+  }
+}
+
+static void line_parabolas_ex(const double* q, int N, double* work, double* qL, double* qR,
+                              double* dq, double* q6, int first_order) {
+  if (first_order) {
+    line_flat(q, N, qL, qR, dq, q6);
+    return;
+  }
   double* dm = work;
   double* face = work + N; /* face[c] = q_{c+1/2} */
   for (int c = 1; c <= N - 2; c++) dm[c] = limited_slope(q[c - 1], q[c], q[c + 1]);
@@ -317,8 +344,9 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
             lb.q2[c] = p[base + st * c];
             lb.r[c] = U[F_RHO][base + st * c];
           }
-          line_parabolas(lb.q, N, lb.work, lb.L, lb.R, lb.D, lb.S);
-          line_parabolas(lb.q2, N, lb.work, lb.L2, lb.R2, lb.D2, lb.S2);
+          const int fo = d->flags & ORACLE_FIRST_ORDER;
+          line_parabolas_ex(lb.q, N, lb.work, lb.L, lb.R, lb.D, lb.S, fo);
+          line_parabolas_ex(lb.q2, N, lb.work, lb.L2, lb.R2, lb.D2, lb.S2, fo);
           /* faces c+1/2 for c in [NG-1, NG+n-1] */
           for (int c = NG - 1; c <= NG + s->n[a] - 1; c++) {
             double rl = lb.r[c], rr = lb.r[c + 1], pl = lb.q2[c], pr = lb.q2[c + 1];
@@ -409,6 +437,10 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
           idx[a] = ia;
           size_t g = gidx(s, idx[0], idx[1], idx[2]);
           size_t db = sb * (size_t)bm, dc = sc * (size_t)cm;
+          if (d->flags & ORACLE_VHAT_1PT) {
+            vt[g] = vel[g];
+            continue;
+          }
           double corners = vel[g + db + dc] + vel[g + db - dc] + vel[g - db + dc] + vel[g - db - dc];
           double edges = vel[g + db] + vel[g - db] + vel[g + dc] + vel[g - dc];
           vt[g] = corners / 16.0 + edges / 8.0 + vel[g] / 4.0;
@@ -440,7 +472,8 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
           size_t base = gidx(s, idx[0], idx[1], idx[2]);
           for (int f = 0; f < NFIELD; f++) {
             for (int c = 0; c < N; c++) lb.q[c] = Us[f][base + st * c];
-            line_parabolas(lb.q, N, lb.work, lb.L, lb.R, lb.D, lb.S);
+            line_parabolas_ex(lb.q, N, lb.work, lb.L, lb.R, lb.D, lb.S,
+                              d->flags & ORACLE_FIRST_ORDER);
             for (int c = NG - 1; c <= NG + s->n[a] - 1; c++) {
               double vh = vhat[base + st * c];
               double y = fabs(vh) * tau / d->h[a];

@@ -36,6 +36,7 @@ struct MarchArgs {
   Partial* partials;
   int tiles_x, tiles_y;  // tile grid of the stage kernels (z tiles = grid / (x * y))
   int any_reflect;       // a reflecting wall exists (its sign flips need register copies)
+  int flags;             // PPML_FIRST_ORDER, PPML_VHAT_1PT
 };
 
 __device__ __forceinline__ double read_tau(const double* dt_dev, double dt_host) {

@@ -148,6 +148,8 @@ int ppml_validate_desc(const ppml_grid_desc* d) {
   if (!(d->cfl > 0.0 && d->cfl < 1.0)) return ppml_fail(PPML_E_INVAL, "cfl = %g not in (0,1)", d->cfl);
   if (d->dtype != PPML_F32 && d->dtype != PPML_F64)
     return ppml_fail(PPML_E_INVAL, "dtype %d is not a ppml_dtype", d->dtype);
+  if (d->flags & ~(int)(PPML_FIRST_ORDER | PPML_VHAT_1PT))
+    return ppml_fail(PPML_E_INVAL, "unknown flags 0x%x", d->flags);
   const long long nc = (long long)n[0] * n[1] * n[2];
   if (nc > (1ll << 31) - 1024) return ppml_fail(PPML_E_INVAL, "grid of %lld cells is too large", nc);
   return PPML_OK;
@@ -180,6 +182,7 @@ MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev)
   A.tiles_y = g->tiles_y;
   A.any_reflect = 0;
   for (int q = 0; q < 6; q++) A.any_reflect |= g->d.bc[q] == PPML_BC_REFLECT;
+  A.flags = g->d.flags;
   return A;
 }
 

@@ -76,6 +76,7 @@ int step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in, ppml_state* u_
     A.g.bc[q] = d->bc[q];
     A.any_reflect |= d->bc[q] == PPML_BC_REFLECT;
   }
+  A.flags = d->flags;
   A.g.nxy = (long long)d->nx * d->ny;
   A.g.ncell = ncell;
   for (int a = 0; a < 3; a++) A.h[a] = d->h[a];

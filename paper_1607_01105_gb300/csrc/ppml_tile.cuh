@@ -12,6 +12,7 @@
 // the domain faces take the unmapped fast path.  The unsplit sums over axes are taken in
 // the order x, y, z.
 #pragma once
+#include "../../include/ppml.h"
 #include "ppml_common.cuh"
 
 namespace ppml {
@@ -83,6 +84,17 @@ __device__ __forceinline__ void line_cell(int ax, int p, int a, int b, int& i, i
 
 // ---------------------------------------------------------------- line pipelines
 
+// The first-order variant's "parabola" of a cell: the constant cell value (Sec. 1.1).
+template <typename T>
+__device__ __forceinline__ Parab<T> flat_parabola(T q) {
+  Parab<T> p;
+  p.L = q;
+  p.R = q;
+  p.D = T(0);
+  p.S = T(0);
+  return p;
+}
+
 // Lagrangian sweep of one field along one line.  q(p) returns the field at position p in
 // [-3, 18]; vh(c) is the face velocity between cells c-1 and c (c = 0..16).  emit(c, d) is
 // called for c = 0..15 with d = th * (F(c+1/2) - F(c-1/2)).
@@ -121,7 +133,7 @@ __device__ __forceinline__ void sweep_lagrangian(QF q, VF vh, T th, double tau, 
 // Eulerian sweep along one line: v(p), pr(p), r(p) give v_a, p and rho at position p.
 // emit(c, dm, dpv, dv) is called for cells c = 0..15 with dm = th (P+ - P-),
 // dpv = th (P+V+ - P-V-), dv = th (V+ - V-).
-template <typename T, typename VF, typename PF, typename RF, typename EF>
+template <typename T, bool FLAT, typename VF, typename PF, typename RF, typename EF>
 __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th, double tau,
                                                double h, EF emit) {
   T va = v(-3), vb = v(-2), pa = pr(-3), pb = pr(-2);
@@ -139,8 +151,8 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
       fpn = face_value(pa, pb, dpa, dpn);
     }
     if (p >= 1) {
-      const Parab<T> Pv = parabola(va, fva, fvn);  // cell p-2
-      const Parab<T> Pq = parabola(pa, fpa, fpn);
+      const Parab<T> Pv = FLAT ? flat_parabola(va) : parabola(va, fva, fvn);  // cell p-2
+      const Parab<T> Pq = FLAT ? flat_parabola(pa) : parabola(pa, fpa, fpn);
       const T rc = r(p - 2);
       if (p >= 2) {
         // face between cells p-3 and p-2
@@ -189,6 +201,14 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// wait until at most N committed groups of this thread are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Field storage of the Lagrangian tile: the 16^3 core (pitches 17, 272) and, per axis, the
 // six halo positions -3..-1, 16..18 of every line (line-major, pitch 257).  Reused as a
@@ -218,7 +238,7 @@ __device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, co
 // The pipeline forms, when position p arrives, the slope at p-1, the face at p-3/2, the
 // parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
 // peeled and the steady state is a rolled loop.
-template <typename T, int MODE>
+template <typename T, int MODE, bool FLAT>
 __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, const T* vh, T th,
                                          double tau, double h, T* acc, bool have_acc,
                                          T* __restrict__ dst, long long gs, int nvalid) {
@@ -236,7 +256,7 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
   qn = core[cs];  // p = 1
   dn = limited_slope(qa, qb, qn);
   T fn = face_value(qa, qb, da, dn);
-  Parab<T> P = parabola(qa, fa, fn);  // cell -1
+  Parab<T> P = FLAT ? flat_parabola(qa) : parabola(qa, fa, fn);  // cell -1
   T PR = P.R, PD = P.D, PS = P.S;
   qa = qb;
   qb = qn;
@@ -245,7 +265,7 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
   qn = core[2 * cs];  // p = 2
   dn = limited_slope(qa, qb, qn);
   fn = face_value(qa, qb, da, dn);
-  P = parabola(qa, fa, fn);  // cell 0
+  P = FLAT ? flat_parabola(qa) : parabola(qa, fa, fn);  // cell 0
   T v = vh[0];
   T y = Prec<T>::courant(tabs(v), tau, h, th);
   T Fp = v * upwind_state(v >= T(0), PR, PD, PS, P.L, P.D, P.S, y);
@@ -260,7 +280,7 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
   auto step = [&](T qnew, int c) {
     const T dnn = limited_slope(qa, qb, qnew);
     const T fnn = face_value(qa, qb, da, dnn);
-    const Parab<T> Pn = parabola(qa, fa, fnn);  // cell c+1
+    const Parab<T> Pn = FLAT ? flat_parabola(qa) : parabola(qa, fa, fnn);  // cell c+1
     const T vv = vh[(c + 1) * TN];              // face between cells c and c+1
     const T yy = Prec<T>::courant(tabs(vv), tau, h, th);
     const T F = vv * upwind_state(vv >= T(0), PR, PD, PS, Pn.L, Pn.D, Pn.S, yy);
@@ -300,6 +320,8 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
+  const bool first_order = (A.flags & PPML_FIRST_ORDER) != 0;
+  const bool one_point = (A.flags & PPML_VHAT_1PT) != 0;
   const bool line_ok = in_domain(g, tg, a, b, 0);
   const int nvalid_z = line_ok ? min(TB, g.n[2] - tg.k0) : 0;
   const long long zline0 =
@@ -358,7 +380,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const T corners = mbox[o + s_b + s_c] + mbox[o + s_b - s_c] + mbox[o - s_b + s_c] +
                         mbox[o - s_b - s_c];
       const T edges = mbox[o + s_b] + mbox[o - s_b] + mbox[o + s_c] + mbox[o - s_c];
-      const T vt = corners / T(16) + edges / T(8) + mbox[o] / T(4);
+      const T vt = one_point ? mbox[o] : corners / T(16) + edges / T(8) + mbox[o] / T(4);
       const T sq = sqrt(rbox[o]);
       if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
       vt_prev = vt;
@@ -427,15 +449,25 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const int cs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
       const T* halo = &S.fld[halo_at(ax, 0, tid)];
       const T* vhl = &S.vh[ax][0][tid];
-      if (ax == 2)
-        lag_line<T, 2>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb], mode == 1,
-                       A.out[f] + zline0, g.nxy, nvalid_z);
+      if (first_order) {
+        if (ax == 2)
+          lag_line<T, 2, true>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
+                               mode == 1, A.out[f] + zline0, g.nxy, nvalid_z);
+        else if (mode == 0)
+          lag_line<T, 0, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
+                               false, nullptr, 0, 0);
+        else
+          lag_line<T, 1, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
+                               false, nullptr, 0, 0);
+      } else if (ax == 2)
+        lag_line<T, 2, false>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
+                              mode == 1, A.out[f] + zline0, g.nxy, nvalid_z);
       else if (mode == 0)
-        lag_line<T, 0>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb], false,
-                       nullptr, 0, 0);
+        lag_line<T, 0, false>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
+                              false, nullptr, 0, 0);
       else
-        lag_line<T, 1>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb], false,
-                       nullptr, 0, 0);
+        lag_line<T, 1, false>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
+                              false, nullptr, 0, 0);
       mode = 1;
       if (ax < 2) __syncthreads();
     }
@@ -561,10 +593,13 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
       }
     };
-    sweep_eulerian<T>([&](int p) { const int o = slab_at(p, a, b); return S.m[o] / S.r[o]; },
-                      [&](int p) { return gm1 * S.p[slab_at(p, a, b)]; },
-                      [&](int p) { return S.r[slab_at(p, a, b)]; }, gamma, th[ax], tau, A.h[ax],
-                      emit);
+    auto vq = [&](int p) { const int o = slab_at(p, a, b); return S.m[o] / S.r[o]; };
+    auto pq = [&](int p) { return gm1 * S.p[slab_at(p, a, b)]; };
+    auto rq = [&](int p) { return S.r[slab_at(p, a, b)]; };
+    if (A.flags & PPML_FIRST_ORDER)
+      sweep_eulerian<T, true>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit);
+    else
+      sweep_eulerian<T, false>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit);
     first = false;
     __syncthreads();
   }

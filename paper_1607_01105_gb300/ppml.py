@@ -23,6 +23,7 @@ PPML_OK, PPML_E_INVAL, PPML_E_CUDA, PPML_E_NONPHYSICAL, PPML_E_TIMEOUT, PPML_E_N
 PPML_F32, PPML_F64 = 0, 1
 OUTFLOW, PERIODIC, REFLECT = 0, 1, 2
 FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
+FIRST_ORDER, VHAT_1PT = 1, 2  # scheme variants (ppml_grid_desc.flags)
 EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppml_eulerian_stage",
             "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
@@ -35,7 +36,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double * 3), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("bc", ctypes.c_int * 6), ("dtype", ctypes.c_int),
-                ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double), ("flags", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -118,7 +119,7 @@ class Grid:
     """Handle over ppml_init_grid / ppml_step / ppml_cfl_dt / ppml_read_diag."""
 
     def __init__(self, n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, u0=None,
-                 vacuum_frac=1e-5, t_end=0.0, stream=None):
+                 vacuum_frac=1e-5, t_end=0.0, stream=None, flags=0):
         d = GridDesc()
         d.nx, d.ny, d.nz = (int(x) for x in n)
         for a in range(3):
@@ -129,6 +130,7 @@ class Grid:
         d.dtype = int(dtype)
         d.vacuum_frac = float(vacuum_frac)
         d.t_end = float(t_end)
+        d.flags = int(flags)
         self.desc = d
         self.n = tuple(int(x) for x in n)
         self.cells = self.n[0] * self.n[1] * self.n[2]
@@ -213,7 +215,8 @@ class Grid:
         return list(ms), n.value
 
 
-def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1e-5, t_end=0.0):
+def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1e-5, t_end=0.0,
+              flags=0):
     d = GridDesc()
     d.nx, d.ny, d.nz = (int(x) for x in n)
     for a in range(3):
@@ -224,6 +227,7 @@ def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1
     d.dtype = int(dtype)
     d.vacuum_frac = float(vacuum_frac)
     d.t_end = float(t_end)
+    d.flags = int(flags)
     return d
 
 

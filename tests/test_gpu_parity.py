@@ -135,6 +135,25 @@ def test_fp64_step_bitwise_equal_to_oracle(case):
     assert diff_s == [0] * 6 and diff == [0] * 6, (diff_s, diff)
 
 
+@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("case", ["rough_outflow_3d", "smooth_mixed_3d", "rough_1d"])
+def test_scheme_variants_fp64_bitwise(case, flags):
+    """First-order (flag 1) and 1-point face-velocity (flag 2) variants: bit for bit with the
+    oracle's variants in FP64, three steps with the device-resident step."""
+    pb = CASES[case]()
+    g = oracle_grid(pb, flags=flags)
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u, flags=flags)
+    ref = pb.u
+    for _ in range(3):
+        ref, dg = oracle.step(g, ref, oracle.cfl_dt(g, ref))
+        grid.step(u, v, 0.0)
+        u, v = v, u
+    got = host(u, shape_of(pb))
+    assert [int(np.count_nonzero(got[f] != ref[f])) for f in range(6)] == [0] * 6
+
+
 @pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_2d", "point_blast_16"])
 def test_step_fp32_single_step(case):
     """One FP32 step from the same (FP32-representable) input as the oracle."""
