@@ -403,13 +403,26 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const long long nx = g.n[0];
       const T* xl = src + (long long)tg.i0 + nx * (tg.j0 + a) + g.nxy * (tg.k0 + b);
       const T* yl = src + (long long)(tg.i0 + a) + nx * tg.j0 + g.nxy * (tg.k0 + b);
+      // three commit groups: core + x halo, y halo, z halo; each sweep waits only for
+      // the group it reads, so the later copies overlap the earlier sweeps
 #pragma unroll
       for (int h = 0; h < HALO_POS; h++) {
         const int p = h < 3 ? h - 3 : TB + h - 3;
         if (act[0]) cp_async_elem(&S.fld[halo_at(0, h, tid)], xl + p);
+      }
+      cp_async_commit();
+#pragma unroll
+      for (int h = 0; h < HALO_POS; h++) {
+        const int p = h < 3 ? h - 3 : TB + h - 3;
         if (act[1]) cp_async_elem(&S.fld[halo_at(1, h, tid)], yl + nx * p);
+      }
+      cp_async_commit();
+#pragma unroll
+      for (int h = 0; h < HALO_POS; h++) {
+        const int p = h < 3 ? h - 3 : TB + h - 3;
         if (act[2]) cp_async_elem(&S.fld[halo_at(2, h, tid)], col + g.nxy * p);
       }
+      cp_async_commit();
     } else {
       for (int it = tid; it < TB * TB * TB; it += TN) {  // core
         const int i = it % TB, j = (it / TB) % TB, k = it / TN;
@@ -437,12 +450,21 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
           *d = load_field(src, f, g, tg, i, j, k);
       }
     }
-    if (async_ok) cp_async_wait_all();
+    if (async_ok && !fast_async) cp_async_wait_all();
+    if (fast_async) cp_async_wait_group<2>();  // core and x halo
     __syncthreads();
     int mode = 0;
 #pragma unroll 1
     for (int ax = 0; ax < 3; ax++) {
       if (!act[ax]) continue;
+      if (fast_async && ax == 1) {  // y halo (the barrier after the x sweep orders it)
+        cp_async_wait_group<1>();
+        __syncthreads();
+      }
+      if (fast_async && ax == 2) {
+        cp_async_wait_group<0>();
+        __syncthreads();
+      }
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
       const int cb = acc_at(li, lj, lk);
