@@ -547,3 +547,151 @@ def test_nine_point_template_reduces_grid_alignment_artifacts():
             resid[rb == k] -= rr[rb == k].mean()
         res[flags] = np.abs(resid[r < 1.1]).mean()
     assert res[oracle.VHAT_1PT] > 1.15 * res[0], res
+
+
+# ------------------------------------------------ isolated Poisson solve (NEXT, S12)
+
+def _table1_case(n, printed_rhs=False):
+    """Table 1 profile on [-1, 1]^3 (sphere inscribed), relative max error of Phi."""
+    from oracle import poisson
+    h = 2.0 / n
+    c = poisson.cell_centres(n, h)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    rho = np.where(r <= 1.0, 2 * r ** 3 - 3 * r ** 2 + 1, 0.0)
+    exact_phi = np.where(r <= 1.0, 4 * math.pi / 15 * r ** 5 - 3 * math.pi / 5 * r ** 4
+                         + 2 * math.pi / 3 * r ** 2 - 3 * math.pi / 5, -4 * math.pi / (15 * r))
+    phi = poisson.solve_isolated(rho, h, 1.0, printed_rhs=printed_rhs)
+    return np.max(np.abs(phi - exact_phi)) / np.max(np.abs(exact_phi))
+
+
+def test_table1_potential_needs_the_corrected_density():
+    """The printed potential solves Delta Phi = 4 pi rho for rho = 2r^3 - 3r^2 + 1, not for
+    the printed 2r^3 - 2r^2 + 1 (the radial Laplacian of each polynomial piece, with Phi and
+    Phi' continuous at r = 1 and the exterior mass 4 pi / 15 equal to the integral of rho)."""
+    P = np.polynomial.Polynomial
+    inner = P([-3 * math.pi / 5, 0, 2 * math.pi / 3, 0, -3 * math.pi / 5, 4 * math.pi / 15])
+    r = np.linspace(0.05, 1.0, 40)
+    lap = inner.deriv(2)(r) + 2.0 * inner.deriv(1)(r) / r
+    assert np.allclose(lap / (4 * math.pi), 2 * r ** 3 - 3 * r ** 2 + 1, rtol=0, atol=1e-12)
+    assert not np.allclose(lap / (4 * math.pi), 2 * r ** 3 - 2 * r ** 2 + 1, atol=1e-3)
+    assert abs(inner(1.0) + 4 * math.pi / 15) < 1e-14           # Phi continuous
+    assert abs(inner.deriv(1)(1.0) - 4 * math.pi / 15) < 1e-14  # Phi' = M / r^2 continuous
+    mass = 4 * math.pi * (P([1, 0, -3, 2]) * P([0, 0, 1])).integ()(1.0)
+    assert abs(mass - 4 * math.pi / 15) < 1e-14
+
+
+def test_multipole_boundary_two_masses_closed_form():
+    """Two unit masses at (+-d, 0, 0): the exact far field is -sum m / |r - r_j|.  The
+    monopole + quadrupole boundary value (MacCullagh, with the 1/2) differs from it by
+    O(R^-5); the monopole alone, or the quadrupole without the 1/2, by O(R^-3)."""
+    from oracle import poisson
+    n, h = 7, 1.0
+    rho = np.zeros((n, n, n))
+    rho[3, 3, 1] = rho[3, 3, 5] = 1.0  # cells centred at x = -2 and +2
+    mom = poisson.multipole_moments(rho, h)
+    assert mom[0] == 2.0 and mom[1] == 0.0 and mom[2] == 8.0 and mom[3] == 8.0
+    dirs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1 / math.sqrt(2), 1 / math.sqrt(2), 0)]
+    errs = {}
+    for R in (40.0, 80.0):
+        for dv in dirs:
+            x, y, z = (R * c for c in dv)
+            exact_phi = -1.0 / math.dist((x, y, z), (-2, 0, 0)) - 1.0 / math.dist((x, y, z), (2, 0, 0))
+            mp = float(poisson.multipole_potential(mom, x, y, z))
+            mono = -2.0 / R
+            no_half = mono + 2.0 * (mp - mono)
+            errs[(R, dv)] = abs(mp - exact_phi)
+            assert abs(mp - exact_phi) <= 0.01 * abs(mono - exact_phi)
+            assert abs(mp - exact_phi) <= 0.01 * abs(no_half - exact_phi)
+        # on the axis, MacCullagh gives -2m/R - 2 m d^2 / R^3
+    assert abs(float(poisson.multipole_potential(mom, 40.0, 0, 0)) - (-2 / 40 - 8 / 40 ** 3)) < 1e-15
+    for dv in dirs:
+        assert errs[(40.0, dv)] / errs[(80.0, dv)] >= 24.0  # R^-5
+
+
+def test_multipole_boundary_random_symmetric_blob():
+    """A point-symmetric random mass distribution (no dipole, no octupole): the boundary
+    value approaches the direct sum as R^-5 in every direction, which needs the products of
+    inertia with the right sign in I_0."""
+    from oracle import poisson
+    rng = np.random.default_rng(5)
+    rho = rng.uniform(0.0, 1.0, size=(5, 7, 9))
+    rho = rho + rho[::-1, ::-1, ::-1]
+    rho[:, :4, :5] *= 3.0  # anisotropic, with products of inertia
+    rho = rho + rho[::-1, ::-1, ::-1]
+    h = 0.5
+    mom = poisson.multipole_moments(rho, h)
+    assert abs(mom[4]) > 0.1 * mom[1]  # I_xy matters
+    z, y, x = np.meshgrid(poisson.cell_centres(5, h), poisson.cell_centres(7, h),
+                          poisson.cell_centres(9, h), indexing="ij")
+    m = rho * h ** 3
+    for dv in rng.normal(size=(6, 3)):
+        dv = dv / np.linalg.norm(dv)
+        e = []
+        for R in (30.0, 60.0):
+            p = R * dv
+            direct = -np.sum(m / np.sqrt((p[0] - x) ** 2 + (p[1] - y) ** 2 + (p[2] - z) ** 2))
+            e.append(abs(float(poisson.multipole_potential(mom, *p)) - direct))
+        assert e[0] / e[1] >= 20.0, e
+
+
+def test_isolated_solve_against_dense_solve_and_the_stencil():
+    """Brute force on a 5x3x4 grid: the 60x60 matrix of the printed 27-point stencil with the
+    shell moved to the right-hand side, solved densely, equals the sine-transform solve; and
+    Phi extended by the multipole shell satisfies the stencil with 4 pi G h^2 (rho + D7 rho/12)
+    (rho = 0 outside) to round-off."""
+    from oracle import poisson
+    rng = np.random.default_rng(8)
+    shape = (4, 3, 5)
+    rho = rng.uniform(0.1, 2.0, size=shape)
+    h, G = 0.3, 1.7
+    w = {1: 4.0 / 9.0, 2: 1.0 / 9.0, 3: 1.0 / 36.0}
+    cells = [(k, j, i) for k in range(4) for j in range(3) for i in range(5)]
+    A = np.zeros((60, 60))
+    for row, (k, j, i) in enumerate(cells):
+        A[row, row] = -38.0 / 9.0
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    nnz = abs(dx) + abs(dy) + abs(dz)
+                    kk, jj, ii = k + dz, j + dy, i + dx
+                    if nnz and 0 <= kk < 4 and 0 <= jj < 3 and 0 <= ii < 5:
+                        A[row, cells.index((kk, jj, ii))] = w[nnz]
+    rhs, shell = poisson.isolated_rhs(rho, h, G)
+    dense = np.linalg.solve(A, rhs.reshape(-1)).reshape(shape)
+    phi = poisson.solve_isolated(rho, h, G)
+    assert np.max(np.abs(phi - dense)) <= 1e-12 * np.max(np.abs(dense))
+    # residual with the shell: ghost values from the expansion at the ghost centres
+    full = shell.copy()
+    full[1:-1, 1:-1, 1:-1] = phi
+    lhs = np.zeros(shape)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                nnz = abs(dx) + abs(dy) + abs(dz)
+                wt = -38.0 / 9.0 if nnz == 0 else w[nnz]
+                lhs += wt * full[1 + dz:5 + dz, 1 + dy:4 + dy, 1 + dx:6 + dx]
+    rp = np.pad(rho, 1)
+    d7 = sum(np.roll(rp, s, axis=a) for a in range(3) for s in (1, -1))[1:-1, 1:-1, 1:-1] - 6 * rho
+    src = 4 * math.pi * G * h * h * (rho + d7 / 12.0)
+    assert np.max(np.abs(lhs - src)) <= 1e-12 * np.max(np.abs(src))
+    # the ghost centres are the cells just outside the grid: the corner ghost of the shell
+    gx = poisson.cell_centres(7, h)[0]
+    assert abs(gx - (-0.5 * 5 * h - 0.5 * h)) < 1e-15
+
+
+def test_isolated_poisson_fourth_order_as_table1():
+    """Table 1: the relative error of the analytic test drops about 16x per doubling (fourth
+    order).  The oracle, on [-1, 1]^3 with the multipole boundary, drops it by 10-30x per
+    doubling and is within a factor 3 of the paper's error at 16^3; with the right-hand side
+    exactly as printed the drop is 4x (second order)."""
+    tab = GOLDEN["poisson_table1"]
+    e = [_table1_case(n) for n in (16, 32, 64)]
+    for a, b in zip(e, e[1:]):
+        assert 10.0 <= a / b <= 30.0, e
+    paper16 = tab["relative_error"][0]
+    assert paper16 / 3.0 <= e[0] <= 3.0 * paper16, (e[0], paper16)
+    for pa, pb in zip(tab["relative_error"], tab["relative_error"][1:]):
+        assert 15.0 <= pa / pb <= 17.0  # the golden values themselves are fourth order
+    p = [_table1_case(n, printed_rhs=True) for n in (16, 32)]
+    assert 3.5 <= p[0] / p[1] <= 4.5, p
