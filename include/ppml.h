@@ -142,6 +142,31 @@ int ppml_step_phi(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const
  * Asynchronous. */
 int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, double G, void* stream);
 
+/* Right-hand side exactly as printed (4 pi G h^2 rho; second-order accurate). */
+#define PPML_POISSON_PRINTED_RHS 1u
+
+/* Isolated-boundary Poisson solve (paper Sec. "The Poisson solver", Stages 1-3, with the
+ * 27-point stencil eq. stencil27point), for a mass distribution that vanishes outside the
+ * grid.  Stage 1: the monopole and quadrupole moments of the cell masses rho h^3 about the
+ * grid centre give the potential on the shell of cells just outside the grid,
+ *   Phi_b = -G M / r - (G/2) (I_x + I_y + I_z - 3 I_0) / r^3
+ * (MacCullagh's formula; the paper prints the quadrupole term without the 1/2), and the shell
+ * values in the stencil of a boundary cell move to the right-hand side.  Stages 2-3: the
+ * Dirichlet problem is diagonal in the sine basis, so the transform is a type-I sine
+ * transform along each axis and the paper's harmonic formula is used with pi j / N replaced
+ * by pi j / (2 (N + 1)), j = 1..N.  Right-hand side 4 pi G h^2 (rho + D7 rho / 12) (D7 the
+ * 7-point second difference, rho = 0 outside the grid), which gives the fourth order the
+ * paper reports in its Table 1; flags = PPML_POISSON_PRINTED_RHS uses 4 pi G h^2 rho.
+ * Geometry: cell (i, j, k) is centred at ((i + 1/2 - nx/2) h, (j + 1/2 - ny/2) h,
+ * (k + 1/2 - nz/2) h); the grid is centred on the origin of the expansion.  Requires
+ * h[0] = h[1] = h[2].  rho, phi: device arrays of nx*ny*nz cells of the grid's type (may
+ * not alias; phi is also the work array).  Moments and shell values are formed in FP64; the
+ * transforms run in the grid's type.  The first call creates cuFFT plans and buffers of
+ * about 2 (N+1)/N x 3 states' worth of the grid's type, kept in the handle.  Asynchronous.
+ * PPML_E_INVAL for bad arguments or unknown flags. */
+int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, double G, unsigned flags,
+                          void* stream);
+
 /* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated) into
  * u_star.  For stage-level checks; same dt convention as ppml_step; does not advance t. */
 int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star, double dt,

@@ -124,6 +124,8 @@ struct ppml_grid {
   cufftHandle fft_fwd, fft_inv;
   void* spec;
   double* tables;
+  // isolated Poisson solve (ppml_poisson.cu)
+  PoissonIso* iso;
 };
 
 int ppml_validate_desc(const ppml_grid_desc* d) {
@@ -343,6 +345,7 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
   }
   if (g->spec) cudaFree(g->spec);
   if (g->tables) cudaFree(g->tables);
+  ppml_iso_free(g->iso);
   delete g;
   return PPML_OK;
 }
@@ -397,6 +400,19 @@ extern "C" int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, d
           : cufftExecC2R(g->fft_inv, (cufftComplex*)g->spec, (cufftReal*)phi);
   if (r != CUFFT_SUCCESS) return ppml_fail(PPML_E_CUDA, "cuFFT inverse failed (%d)", (int)r);
   return PPML_OK;
+}
+
+extern "C" int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, double G,
+                                     unsigned flags, void* stream) {
+  ppml_clear_error();
+  if (!g || !rho || !phi) return ppml_fail(PPML_E_INVAL, "grid, rho or phi is NULL");
+  if (rho == phi) return ppml_fail(PPML_E_INVAL, "rho and phi alias");
+  if (!isfinite(G)) return ppml_fail(PPML_E_INVAL, "G is not finite");
+  if (flags & ~PPML_POISSON_PRINTED_RHS) return ppml_fail(PPML_E_INVAL, "unknown flags 0x%x", flags);
+  for (int a = 1; a < 3; a++)
+    if (fabs(g->d.h[a] - g->d.h[0]) > 1e-12 * g->d.h[0])
+      return ppml_fail(PPML_E_INVAL, "the 27-point solve needs equal cell sizes");
+  return ppml_iso_solve(&g->iso, &g->d, rho, phi, G, flags, (cudaStream_t)stream);
 }
 
 extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, void* stream) {

@@ -14,3 +14,9 @@ int ppml_check_launch(const char* what);
 // Argument checks shared by the entry points (defined in ppml_grid.cu).
 int ppml_validate_desc(const ppml_grid_desc* d);
 int ppml_validate_state(const ppml_state* u, const char* what);
+
+// Isolated-boundary Poisson solver state (ppml_poisson.cu); created on the first solve.
+struct PoissonIso;
+int ppml_iso_solve(PoissonIso** state, const ppml_grid_desc* d, const void* rho, void* phi,
+                   double G, unsigned flags, cudaStream_t st);
+void ppml_iso_free(PoissonIso* s);

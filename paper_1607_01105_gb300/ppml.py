@@ -28,8 +28,9 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
-            "ppml_poisson_periodic")
+            "ppml_poisson_periodic", "ppml_poisson_isolated")
 NOALLOC_MAX_CELLS = 262144
+POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
 
 class GridDesc(ctypes.Structure):
@@ -70,6 +71,7 @@ _lib.ppml_last_error.restype = ctypes.c_char_p
 _lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
 _lib.ppml_step_phi.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), _vp, ctypes.c_double, _vp]
 _lib.ppml_poisson_periodic.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp]
+_lib.ppml_poisson_isolated.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_uint, _vp]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -179,6 +181,15 @@ class Grid:
             if not t.is_cuda or t.dtype != self.tdtype or t.numel() != self.cells or not t.is_contiguous():
                 raise ValueError("rho and phi must be contiguous CUDA tensors of the grid's dtype and size")
         _check(_lib.ppml_poisson_periodic(self._h, rho.data_ptr(), phi.data_ptr(), float(G), _stream(stream)))
+
+    def poisson_isolated(self, rho, phi, G=1.0, printed_rhs=False, stream=None):
+        """Isolated-boundary 27-point Poisson solve of rho into phi (multipole shell, sine
+        transforms); the grid is centred on the origin of the expansion."""
+        for t in (rho, phi):
+            if not t.is_cuda or t.dtype != self.tdtype or t.numel() != self.cells or not t.is_contiguous():
+                raise ValueError("rho and phi must be contiguous CUDA tensors of the grid's dtype and size")
+        _check(_lib.ppml_poisson_isolated(self._h, rho.data_ptr(), phi.data_ptr(), float(G),
+                                          POISSON_PRINTED_RHS if printed_rhs else 0, _stream(stream)))
 
     def eulerian_stage(self, u_in, u_star, dt, stream=None):
         a = _state(u_in, self.tdtype, self.cells)

@@ -81,3 +81,5 @@ def test_invalid_descriptors_rejected_on_host(built):
     assert lib.ppml_batch_init(2, nc, hh, te, 1.4, 1.4, 0.0, 0, ctypes.byref(h)) == ppml.PPML_E_INVAL
     assert lib.ppml_step(None, None, None, ctypes.c_double(0.1), None) == ppml.PPML_E_INVAL
     assert lib.ppml_free_grid(None) == ppml.PPML_OK
+    assert lib.ppml_poisson_isolated(None, None, None, 1.0, 0, None) == ppml.PPML_E_INVAL
+    assert lib.ppml_poisson_periodic(None, None, None, 1.0, None) == ppml.PPML_E_INVAL
