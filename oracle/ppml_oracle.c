@@ -86,6 +86,7 @@ typedef struct {
 
 typedef struct {
   int n[3], N[3];
+  int g[3];     /* ghost layers per side: NG on axes with more than one cell, else 0 */
   size_t cells; /* N0*N1*N2 */
 } gshape;
 
@@ -94,7 +95,8 @@ static gshape make_shape(const oracle_desc* d) {
   s.cells = 1;
   for (int a = 0; a < 3; a++) {
     s.n[a] = d->n[a];
-    s.N[a] = d->n[a] + 2 * NG;
+    s.g[a] = d->n[a] > 1 ? NG : 0; /* nothing reads ghosts along a single-cell axis */
+    s.N[a] = d->n[a] + 2 * s.g[a];
     s.cells *= (size_t)s.N[a];
   }
   return s;
@@ -115,7 +117,7 @@ static void scatter_interior(const gshape* s, const double* src, double* dst) {
   for (int k = 0; k < s->n[2]; k++)
     for (int j = 0; j < s->n[1]; j++)
       for (int i = 0; i < s->n[0]; i++)
-        dst[gidx(s, i + NG, j + NG, k + NG)] =
+        dst[gidx(s, i + s->g[0], j + s->g[1], k + s->g[2])] =
             src[(size_t)i + (size_t)s->n[0] * ((size_t)j + (size_t)s->n[1] * (size_t)k)];
 }
 
@@ -124,7 +126,7 @@ static void gather_interior(const gshape* s, const double* src, double* dst) {
     for (int j = 0; j < s->n[1]; j++)
       for (int i = 0; i < s->n[0]; i++)
         dst[(size_t)i + (size_t)s->n[0] * ((size_t)j + (size_t)s->n[1] * (size_t)k)] =
-            src[gidx(s, i + NG, j + NG, k + NG)];
+            src[gidx(s, i + s->g[0], j + s->g[1], k + s->g[2])];
 }
 
 /* Interior coordinate that a ghost coordinate c (c < 0 or c >= n) copies from, and the
@@ -155,14 +157,14 @@ static void fill_ghosts(const gshape* s, const oracle_desc* d, double* q, int fi
         int idx[3];
         idx[a] = 0; idx[b] = ib; idx[c] = ic;
         size_t base = gidx(s, idx[0], idx[1], idx[2]);
-        for (int g = 0; g < NG; g++) {
-          int ghosts[2] = {g - NG, s->n[a] + g}; /* interior coords of a low and a high ghost */
+        for (int g = 0; g < s->g[a]; g++) {
+          int ghosts[2] = {g - s->g[a], s->n[a] + g}; /* interior coords of a low and a high ghost */
           for (int side = 0; side < 2; side++) {
             int flip;
             int src = bc_source(ghosts[side], s->n[a], d->bc[2 * a], d->bc[2 * a + 1], &flip);
-            double v = q[base + st * (size_t)(src + NG)];
+            double v = q[base + st * (size_t)(src + s->g[a])];
             if (flip && field == F_MX + a) v = -v;
-            q[base + st * (size_t)(ghosts[side] + NG)] = v;
+            q[base + st * (size_t)(ghosts[side] + s->g[a])] = v;
           }
         }
       }
@@ -334,8 +336,8 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
       linebuf lb;
       lb_alloc(&lb, N);
 #pragma omp for schedule(static)
-      for (int ic = NG; ic < NG + s->n[cax]; ic++)
-        for (int ib = NG; ib < NG + s->n[b]; ib++) {
+      for (int ic = s->g[cax]; ic < s->g[cax] + s->n[cax]; ic++)
+        for (int ib = s->g[b]; ib < s->g[b] + s->n[b]; ib++) {
           int idx[3];
           idx[a] = 0; idx[b] = ib; idx[cax] = ic;
           size_t base = gidx(s, idx[0], idx[1], idx[2]);
@@ -370,9 +372,9 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
   }
   /* S3 update of the interior */
 #pragma omp parallel for schedule(static)
-  for (int k = NG; k < NG + s->n[2]; k++)
-    for (int j = NG; j < NG + s->n[1]; j++)
-      for (int i = NG; i < NG + s->n[0]; i++) {
+  for (int k = s->g[2]; k < s->g[2] + s->n[2]; k++)
+    for (int j = s->g[1]; j < s->g[1] + s->n[1]; j++)
+      for (int i = s->g[0]; i < s->g[0] + s->n[0]; i++) {
         size_t g = gidx(s, i, j, k);
         double rho = U[F_RHO][g];
         double m[3], en = U[F_EN][g] - dPV[g];
@@ -448,8 +450,8 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
       }
     /* faces along a: v hat at c+1/2 for the interior lines */
 #pragma omp parallel for schedule(static)
-    for (int io = NG; io < NG + s->n[lo]; io++)
-      for (int ii = NG; ii < NG + s->n[li]; ii++) {
+    for (int io = s->g[lo]; io < s->g[lo] + s->n[lo]; io++)
+      for (int ii = s->g[li]; ii < s->g[li] + s->n[li]; ii++) {
         int idx[3];
         idx[a] = 0; idx[lo] = io; idx[li] = ii;
         size_t base = gidx(s, idx[0], idx[1], idx[2]);
@@ -465,8 +467,8 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
       linebuf lb;
       lb_alloc(&lb, N);
 #pragma omp for schedule(static)
-      for (int io = NG; io < NG + s->n[lo]; io++)
-        for (int ii = NG; ii < NG + s->n[li]; ii++) {
+      for (int io = s->g[lo]; io < s->g[lo] + s->n[lo]; io++)
+        for (int ii = s->g[li]; ii < s->g[li] + s->n[li]; ii++) {
           int idx[3];
           idx[a] = 0; idx[lo] = io; idx[li] = ii;
           size_t base = gidx(s, idx[0], idx[1], idx[2]);
@@ -492,9 +494,9 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
     }
   }
 #pragma omp parallel for schedule(static)
-  for (int k = NG; k < NG + s->n[2]; k++)
-    for (int j = NG; j < NG + s->n[1]; j++)
-      for (int i = NG; i < NG + s->n[0]; i++) {
+  for (int k = s->g[2]; k < s->g[2] + s->n[2]; k++)
+    for (int j = s->g[1]; j < s->g[1] + s->n[1]; j++)
+      for (int i = s->g[0]; i < s->g[0] + s->n[0]; i++) {
         size_t g = gidx(s, i, j, k);
         for (int f = 0; f < NFIELD; f++) Un[f][g] = Us[f][g] - div[f][g];
       }
@@ -633,9 +635,9 @@ int oracle_step(const oracle_desc* d, double* const u_in[NFIELD], double* const 
   /* S8, serial counters */
   double rho_vac = d->vacuum_frac * d->rho_mean;
   long long cnt[4] = {0, 0, 0, 0};
-  for (int k = NG; k < NG + s.n[2]; k++)
-    for (int j = NG; j < NG + s.n[1]; j++)
-      for (int i = NG; i < NG + s.n[0]; i++) {
+  for (int k = s.g[2]; k < s.g[2] + s.n[2]; k++)
+    for (int j = s.g[1]; j < s.g[1] + s.n[1]; j++)
+      for (int i = s.g[0]; i < s.g[0] + s.n[0]; i++) {
         size_t g = gidx(&s, i, j, k);
         double u[NFIELD];
         for (int f = 0; f < NFIELD; f++) u[f] = Un[f][g];

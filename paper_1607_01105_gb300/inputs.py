@@ -82,6 +82,18 @@ def sod_1d(n=256, row=1, gamma=1.4, cfl=0.4) -> Problem:
                    {"states": (rl, ul, pl, rr, ur, pr), "x_split": xs})
 
 
+def two_blast_waves(n=2400, gamma=1.4, cfl=0.4, t_end=0.038) -> Problem:
+    """Two interacting blast waves on [0, 1] (Sec. 'Two Interacting Blast Waves'): rho = 1,
+    v = 0, p = 1000 / 0.01 / 100 split at x = 0.1 and 0.9, reflecting walls, 2400 cells.
+    The paper shows the result without its time; t_end is the time of the original test."""
+    h = 1.0 / n
+    x = _centres(n, h, 0.0)
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))[None, None, :]
+    rho = np.ones_like(p)
+    return Problem(f"two_blast_waves_{n}", (n, 1, 1), (h, 1.0, 1.0), (0.0, 0.0, 0.0), gamma, cfl,
+                   (REFLECT,) * 6, t_end, conserved(rho, 0.0, 0.0, 0.0, p, gamma), {})
+
+
 def planar_sod_3d(n=128, gamma=1.4, cfl=0.2) -> Problem:
     rl, ul, pl, rr, ur, pr, xs, t = SOD_TABLE2[1]
     h = 1.0 / n

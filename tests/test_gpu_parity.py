@@ -260,6 +260,23 @@ def test_config1_sod_fp64_and_fp32():
         assert d32["sums"][f] == pytest.approx(dgo["sums"][f], rel=1e-6)
 
 
+def test_two_blast_waves_reflecting_fp64_fp32():
+    """Two interacting blast waves (2400 cells, reflecting walls, about 10^4 steps to
+    t = 0.038) with the device-resident step: FP64 identical to the oracle run, FP32 within
+    1e-3 (rho, rho eps) with mass and energy sums within 1e-6."""
+    pb = inputs.two_blast_waves()
+    g = oracle_grid(pb)
+    ref, t, steps_o, dgo = oracle.run(g, pb.u, pb.t_end)
+    got, d, steps = run_gpu(pb, F64)
+    assert steps == steps_o and d["t"] == pytest.approx(pb.t_end, rel=1e-14)
+    compare(got, ref, TOL64)
+    got32, d32, steps32 = run_gpu(pb, F32)
+    assert d32["t"] == pytest.approx(pb.t_end, rel=1e-12)
+    compare(got32, ref, 1e-3, fields=(0, 5))
+    for f in (0, 4):
+        assert d32["sums"][f] == pytest.approx(dgo["sums"][f], rel=1e-6)
+
+
 def test_config2_planar_128_fp64_fp32():
     """3D planar shock tube 128^3 (outflow x, periodic y z): parity over 3 steps, and the
     GPU output stays exactly uniform in y and z."""

@@ -549,6 +549,37 @@ def test_nine_point_template_reduces_grid_alignment_artifacts():
     assert res[oracle.VHAT_1PT] > 1.15 * res[0], res
 
 
+# ------------------------------------------------------- reflecting walls (NEXT)
+
+def _local_peaks(q, x, order=40):
+    return [(x[i], q[i]) for i in range(order, len(q) - order)
+            if q[i] == q[i - order:i + order + 1].max()]
+
+
+@pytest.mark.slow
+def test_two_interacting_blast_waves():
+    """The paper's two-blast-wave test (2400 cells, reflecting walls): the density peak about
+    6.5 near x = 0.76, the precursor about 1.0 near x = 0.86 and velocity peaks near x = 0.65
+    and 0.86, as printed; reflecting walls conserve mass and total energy to round-off."""
+    gv = GOLDEN["two_blast_waves"]
+    pb = inputs.two_blast_waves(gv["cells"])
+    g = grid_of(pb)
+    u, t, steps, dg = oracle.run(g, pb.u, pb.t_end)
+    assert t == pb.t_end and dg["n_nonphys"] == 0
+    x = (np.arange(pb.n[0]) + 0.5) * pb.h[0]
+    rho = u[0].ravel()
+    v = u[1].ravel() / rho
+    i = int(np.argmax(rho))
+    assert abs(rho[i] - gv["shock"]["rho"]) <= 0.3 and abs(x[i] - gv["shock"]["x"]) <= 0.02
+    pre = [(xx, q) for xx, q in _local_peaks(rho, x) if abs(xx - gv["precursor"]["x"]) <= 0.015]
+    assert pre and abs(pre[0][1] - gv["precursor"]["rho"]) <= 0.1, pre
+    vp = [xx for xx, q in _local_peaks(v, x) if q > 1.0]
+    assert len(vp) == 2 and all(abs(a - b) <= 0.015 for a, b in zip(vp, gv["velocity_peaks_x"])), vp
+    s0 = oracle.diagnostics(g, pb.u)["sums"]
+    assert dg["sums"][0] == pytest.approx(s0[0], rel=1e-13)
+    assert dg["sums"][4] == pytest.approx(s0[4], rel=1e-13)
+
+
 # ------------------------------------------------ isolated Poisson solve (NEXT, S12)
 
 def _table1_case(n, printed_rhs=False):
