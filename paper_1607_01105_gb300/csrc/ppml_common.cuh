@@ -144,6 +144,25 @@ __device__ __forceinline__ void cell_speeds(const T u[6], T gamma, T gm1, T& vma
   }
 }
 
+// FP32 form for the stage kernels: one approximate reciprocal of rho, |v| = |m| / rho.
+__device__ __forceinline__ void cell_speeds_f32(const float u[6], float gamma, float gm1,
+                                                float& vmax, float& cmax,
+                                                unsigned long long& nbad) {
+  const float rho = u[0];
+  const float ir = rcp_approx(rho);
+  const float v = sqrt_approx(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir;
+  const float c = sqrt_approx(gamma * gm1 * u[5] * ir);
+  bool ok = rho > 0.f && u[5] > 0.f;
+#pragma unroll
+  for (int f = 0; f < 6; f++) ok = ok && isfinite(u[f]);
+  if (ok) {
+    vmax = fmaxf(vmax, v);
+    cmax = fmaxf(cmax, c);
+  } else {
+    nbad++;
+  }
+}
+
 // ------------------------------------------------------------------ standalone diagnostics
 
 template <typename T>

@@ -170,6 +170,36 @@ __device__ __forceinline__ int energy_correction(double u[6], double rho_vac) {
   return 0;
 }
 
+// ------------------------------------------------------- approximate FP32 operations
+// PTX rcp.approx.f32 / sqrt.approx.f32 (relative error about 2^-23, one special-function
+// instruction each).  The FP32 stage kernels use them where the result only feeds
+// tolerance-checked FP32 arithmetic (velocities m / rho, Roe weights, the acoustic face
+// constants, signal speeds); the FP64 instantiation never does.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// FP32 face constants (as face_constants) from the adjacent cell values and their square
+// roots sl, sr (computed once per cell by the caller): lambda = sqrt(gamma B / A) and
+// Z = sqrt(gamma A B) / S = lambda A / S.  Also returns 1 / (2 Z) for the velocity.
+__device__ __forceinline__ void face_constants_f32(float rl, float rr, float sl, float sr,
+                                                   float pl, float pr, float gamma, float& lam,
+                                                   float& Z, float& half_rz) {
+  const float A = rl * sl + rr * sr;
+  const float B = pl * sl + pr * sr;
+  const float S = sl + sr;
+  lam = sqrt_approx(gamma * B * rcp_approx(A));
+  Z = lam * A * rcp_approx(S);
+  half_rz = 0.5f * rcp_approx(Z);
+}
+
 // ---------------------------------------------------------- compensated FP32 helpers
 // Error-free transformations (Knuth TwoSum; FMA-based TwoProduct).  Used where the
 // paper's quantity is a small difference of large totals so that the FP32 path keeps
@@ -193,9 +223,10 @@ __device__ __forceinline__ float internal_energy_ff(float rho, float mx, float m
   two_sum(s, p3, hi, t2);
   const float lo = ((t1 + t2) + (e1 + e2)) + e3;  // |m|^2 = hi + lo
   const float r2 = 2.0f * rho;
-  const float q = hi / r2;
-  const float rem = fmaf(-q, r2, hi) + lo;  // exact remainder of hi plus lo
-  const float ql = rem / r2;                // |m|^2/(2 rho) = q + ql
+  const float ir2 = rcp_approx(r2);
+  const float q = hi * ir2;
+  const float rem = fmaf(-q, r2, hi) + lo;  // remainder of hi (exact to 2^-46) plus lo
+  const float ql = rem * ir2;               // |m|^2/(2 rho) = q + ql
   float d, de;
   two_sum(en, -q, d, de);
   return d + (de - ql);
@@ -225,10 +256,11 @@ template <>
 __device__ __forceinline__ int correct_energy<double>(double u[6], double rho_vac) {
   return energy_correction(u, rho_vac);
 }
-template <>
-__device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac) {
+// rho_vac_up = rho_vac rounded up to float: for any float x, x < rho_vac_up exactly when
+// x < rho_vac (no float lies in [rho_vac, rho_vac_up) other than rho_vac itself).
+__device__ __forceinline__ int correct_energy_f32(float u[6], float rho_vac_up, double rho_vac) {
   const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-  if ((double)u[0] < rho_vac && m2 > 0.f) {
+  if (u[0] < rho_vac_up && m2 > 0.f) {
     double d[6] = {u[0], u[1], u[2], u[3], u[4], u[5]};
     energy_correction(d, rho_vac);
     u[1] = (float)d[1];
@@ -240,6 +272,10 @@ __device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac)
   const float e = internal_energy_ff(u[0], u[1], u[2], u[3], u[4]);
   if (e > 0.f) u[5] = e;
   return 0;
+}
+template <>
+__device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac) {
+  return correct_energy_f32(u, __double2float_ru(rho_vac), rho_vac);
 }
 
 // Boundary handling by index mapping: interior coordinate read for coordinate c of an

@@ -141,6 +141,7 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
   T vR = T(0), vD = T(0), vS = T(0), pR = T(0), pD = T(0), pS = T(0);
   T Vp = T(0), Pp = T(0);
   T rprev = T(0), pprev = T(0);  // rho, p of cell p-3
+  T sprev = T(0);                // FP32: sqrt(rho) of cell p-3
 #pragma unroll
   for (int p = -1; p <= TB + 2; p++) {
     const T vn = v(p), pn = pr(p);
@@ -154,7 +155,22 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
       const Parab<T> Pv = FLAT ? flat_parabola(va) : parabola(va, fva, fvn);  // cell p-2
       const Parab<T> Pq = FLAT ? flat_parabola(pa) : parabola(pa, fpa, fpn);
       const T rc = r(p - 2);
-      if (p >= 2) {
+      if constexpr (sizeof(T) == 4) {
+        const float sc = sqrt_approx(rc);
+        if (p >= 2) {  // face between cells p-3 and p-2
+          float lam, Z, hrz;
+          face_constants_f32(rprev, rc, sprev, sc, pprev, pa, gamma, lam, Z, hrz);
+          const float y = lam * th;
+          const float vls = avg_right(vR, vD, vS, y), vrs = avg_left(Pv.L, Pv.D, Pv.S, y);
+          const float pls = avg_right(pR, pD, pS, y), prs = avg_left(Pq.L, Pq.D, Pq.S, y);
+          const float V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
+          const float P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
+          if (p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
+          Vp = V;
+          Pp = P;
+        }
+        sprev = sc;
+      } else if (p >= 2) {
         // face between cells p-3 and p-2
         T lam, Z;
         face_constants(rprev, rc, pprev, pa, gamma, lam, Z);
@@ -229,6 +245,33 @@ __device__ __forceinline__ int halo_at(int ax, int h, int line) {
 }
 __device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, coords -1..16
   return (i + 1) + 18 * (j + 1) + 324 * (k + 1);
+}
+
+// Asynchronous copy of one field over the dense 18^3 box (tile coordinates -1..16) of an
+// interior tile: thread tid copies elements tid, tid + 256, ...; the box coordinates and
+// the global offset advance by 256 = 14 * 18 + 4 elements per copy with carries.
+template <typename T>
+__device__ __forceinline__ void stage_box_fast(T* box, const T* __restrict__ src,
+                                               const GridGeom& g, const TileGeom& tg, int tid) {
+  int i = tid % 18, j = (tid / 18) % 18;
+  const long long nx = g.n[0];
+  long long off = (long long)(tg.i0 - 1 + i) + nx * (tg.j0 - 1 + j) + g.nxy * (tg.k0 - 1 + tid / 324);
+  for (int it = tid; it < 18 * 18 * 18; it += TN) {
+    cp_async_elem(&box[it], src + off);
+    i += 4;
+    off += 4;
+    if (i >= 18) {
+      i -= 18;
+      off += nx - 18;
+      j++;
+    }
+    j += 14;
+    off += 14 * nx;
+    if (j >= 18) {
+      j -= 18;
+      off += g.nxy - 18 * nx;
+    }
+  }
 }
 
 // One line of the Lagrangian stage for any axis.  Field values: core[p cs] for p in
@@ -336,35 +379,36 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   T* mbox = smem_t + 5832;  // m_a, then v_a
   static_assert(2 * 5832 <= LAG_FIELD + ACC, "template boxes must fit in fld + acc");
   const bool fast_async = async_ok && tg.fast;
-  {
-    // rho once for all three axes
+  if (fast_async) {
+    stage_box_fast(rbox, A.u[0], g, tg, tid);  // rho once for all three axes
+  } else {
     for (int it = tid; it < 18 * 18 * 18; it += TN) {
       const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
       int fl;
-      const long long c = cell_index(g, tg, i, j, k, fl);
-      if (fast_async)
-        cp_async_elem(&rbox[it], A.u[0] + c);
-      else
-        rbox[it] = A.u[0][c];
+      rbox[it] = A.u[0][cell_index(g, tg, i, j, k, fl)];
     }
   }
 #pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
-    for (int it = tid; it < 18 * 18 * 18; it += TN) {
-      const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
-      int fl;
-      const long long c = cell_index(g, tg, i, j, k, fl);
-      if (fast_async) {
-        cp_async_elem(&mbox[it], A.u[1 + ax] + c);
-      } else {
-        const T m = A.u[1 + ax][c];
+    if (fast_async) {
+      stage_box_fast(mbox, A.u[1 + ax], g, tg, tid);
+    } else {
+      for (int it = tid; it < 18 * 18 * 18; it += TN) {
+        const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
+        int fl;
+        const T m = A.u[1 + ax][cell_index(g, tg, i, j, k, fl)];
         mbox[it] = ((fl >> ax) & 1) ? -m : m;
       }
     }
     if (fast_async) cp_async_wait_all();
     __syncthreads();
-    for (int it = tid; it < 18 * 18 * 18; it += TN) mbox[it] = mbox[it] / rbox[it];
+    for (int it = tid; it < 18 * 18 * 18; it += TN) {
+      if constexpr (sizeof(T) == 4)
+        mbox[it] = mbox[it] * rcp_approx(rbox[it]);
+      else
+        mbox[it] = mbox[it] / rbox[it];
+    }
     __syncthreads();
     // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
     const int s_ax = ax == 0 ? 1 : (ax == 1 ? 18 : 324);
@@ -381,6 +425,13 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
                         mbox[o - s_b - s_c];
       const T edges = mbox[o + s_b] + mbox[o - s_b] + mbox[o + s_c] + mbox[o - s_c];
       const T vt = one_point ? mbox[o] : corners / T(16) + edges / T(8) + mbox[o] / T(4);
+      if constexpr (sizeof(T) == 4) {
+        const float sq = sqrt_approx(rbox[o]);
+        if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) * rcp_approx(sq + sq_prev);
+        vt_prev = vt;
+        sq_prev = sq;
+        continue;
+      }
       const T sq = sqrt(rbox[o]);
       if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
       vt_prev = vt;
@@ -403,8 +454,6 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const long long nx = g.n[0];
       const T* xl = src + (long long)tg.i0 + nx * (tg.j0 + a) + g.nxy * (tg.k0 + b);
       const T* yl = src + (long long)(tg.i0 + a) + nx * tg.j0 + g.nxy * (tg.k0 + b);
-      // three commit groups: core + x halo, y halo, z halo; each sweep waits only for
-      // the group it reads, so the later copies overlap the earlier sweeps
 #pragma unroll
       for (int h = 0; h < HALO_POS; h++) {
         const int p = h < 3 ? h - 3 : TB + h - 3;
@@ -507,19 +556,26 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   sums.init();
   T vmax = T(0), cmax = T(0);
   unsigned long long nvac = 0, nbad = 0;
+  const float rho_vac_up = __double2float_ru(A.rho_vac);
 #pragma unroll 2
   for (int c = 0; c < nvalid_z; c++) {
     const long long idx = zline0 + g.nxy * c;
     T u[6];
 #pragma unroll
     for (int f = 0; f < 6; f++) u[f] = A.out[f][idx];
-    nvac += correct_energy<T>(u, A.rho_vac);
+    if constexpr (sizeof(T) == 4)
+      nvac += correct_energy_f32(u, rho_vac_up, A.rho_vac);
+    else
+      nvac += correct_energy<T>(u, A.rho_vac);
     A.out[1][idx] = u[1];
     A.out[2][idx] = u[2];
     A.out[3][idx] = u[3];
     A.out[5][idx] = u[5];
     sums.add(u);
-    cell_speeds<T>(u, gamma, gm1, vmax, cmax, nbad);
+    if constexpr (sizeof(T) == 4)
+      cell_speeds_f32(u, gamma, gm1, vmax, cmax, nbad);
+    else
+      cell_speeds<T>(u, gamma, gm1, vmax, cmax, nbad);
   }
   double sd[6];
   sums.get(sd);
@@ -615,7 +671,13 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
       }
     };
-    auto vq = [&](int p) { const int o = slab_at(p, a, b); return S.m[o] / S.r[o]; };
+    auto vq = [&](int p) {
+      const int o = slab_at(p, a, b);
+      if constexpr (sizeof(T) == 4)
+        return S.m[o] * rcp_approx(S.r[o]);
+      else
+        return S.m[o] / S.r[o];
+    };
     auto pq = [&](int p) { return gm1 * S.p[slab_at(p, a, b)]; };
     auto rq = [&](int p) { return S.r[slab_at(p, a, b)]; };
     if (A.flags & PPML_FIRST_ORDER)

@@ -91,7 +91,7 @@ def two_blast_waves(n=2400, gamma=1.4, cfl=0.4, t_end=0.038) -> Problem:
     p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))[None, None, :]
     rho = np.ones_like(p)
     return Problem(f"two_blast_waves_{n}", (n, 1, 1), (h, 1.0, 1.0), (0.0, 0.0, 0.0), gamma, cfl,
-                   (REFLECT,) * 6, t_end, conserved(rho, 0.0, 0.0, 0.0, p, gamma), {})
+                   (REFLECT, REFLECT, OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW), t_end, conserved(rho, 0.0, 0.0, 0.0, p, gamma), {})
 
 
 def planar_sod_3d(n=128, gamma=1.4, cfl=0.2) -> Problem:
