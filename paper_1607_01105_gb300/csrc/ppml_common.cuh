@@ -43,6 +43,23 @@ __device__ __forceinline__ double read_tau(const double* dt_dev, double dt_host)
   return dt_dev ? *dt_dev : dt_host;
 }
 
+// The step size and tau / h per axis, formed by one thread of the CTA (three FP64
+// divisions per CTA instead of per thread) and shared.  Contains a CTA barrier.
+__device__ __forceinline__ void cta_step_constants(const double* dt_dev, double dt_host,
+                                                   const double h[3], double out[4]) {
+  __shared__ double s[4];
+  if (threadIdx.x == 0) {
+    const double tau = read_tau(dt_dev, dt_host);
+    s[0] = tau;
+    s[1] = tau / h[0];
+    s[2] = tau / h[1];
+    s[3] = tau / h[2];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; q++) out[q] = s[q];
+}
+
 // ------------------------------------------------------------------ block reduction
 
 template <int NTHREADS>
@@ -63,6 +80,70 @@ __device__ __forceinline__ void block_reduce_store(double s[6], double vmax, dou
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     for (int f = 0; f < 6; f++) sh[w][f] = s[f];
+    sh[w][6] = vmax;
+    sh[w][7] = cmax;
+    shc[w][0] = nvac;
+    shc[w][1] = nbad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial p;
+    for (int f = 0; f < 6; f++) p.s[f] = 0.0;
+    p.vmax = 0.0;
+    p.cmax = 0.0;
+    p.nvac = 0;
+    p.nbad = 0;
+    for (int q = 0; q < NTHREADS / 32; q++) {
+      for (int f = 0; f < 6; f++) p.s[f] += sh[q][f];
+      p.vmax = fmax(p.vmax, sh[q][6]);
+      p.cmax = fmax(p.cmax, sh[q][7]);
+      p.nvac += shc[q][0];
+      p.nbad += shc[q][1];
+    }
+    out[blockIdx.x] = p;
+  }
+}
+
+// (hi, lo) += (bh, bl) in double-float (TwoSum of the high parts, then renormalised).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e += lo + bl;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// block_reduce_store for the FP32 stage kernels: the warp level of the sums runs in
+// double-float (FP32 operations only), the maxima in float (exact) and the counters in
+// 32 bits; warp leaders convert to double and thread 0 folds the warps in a fixed order.
+template <int NTHREADS>
+__device__ __forceinline__ void block_reduce_store_f32(const float hi_in[6], const float lo_in[6],
+                                                       float vmax, float cmax, unsigned nvac,
+                                                       unsigned nbad, Partial* out) {
+  float hi[6], lo[6];
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    hi[f] = hi_in[f];
+    lo[f] = lo_in[f];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      const float bh = __shfl_down_sync(0xffffffffu, hi[f], o);
+      const float bl = __shfl_down_sync(0xffffffffu, lo[f], o);
+      ff_add(hi[f], lo[f], bh, bl);
+    }
+    vmax = fmaxf(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    cmax = fmaxf(cmax, __shfl_down_sync(0xffffffffu, cmax, o));
+    nvac += __shfl_down_sync(0xffffffffu, nvac, o);
+    nbad += __shfl_down_sync(0xffffffffu, nbad, o);
+  }
+  __shared__ double sh[NTHREADS / 32][8];
+  __shared__ unsigned long long shc[NTHREADS / 32][2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    for (int f = 0; f < 6; f++) sh[w][f] = (double)hi[f] + (double)lo[f];
     sh[w][6] = vmax;
     sh[w][7] = cmax;
     shc[w][0] = nvac;

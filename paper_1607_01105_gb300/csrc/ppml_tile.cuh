@@ -345,7 +345,7 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
     da = dnn;
     fa = fnn;
   };
-#pragma unroll 1
+#pragma unroll 2
   for (int c = 0; c < TB - 3; c++) step(core[(c + 3) * cs], c);
 #pragma unroll 1
   for (int c = TB - 3; c < TB; c++) step(halo[(c - TB + 6) * SLP], c);
@@ -359,8 +359,10 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
-  const double tau = read_tau(A.dt_dev, A.dt_host);
-  const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
+  double stc[4];
+  cta_step_constants(A.dt_dev, A.dt_host, A.h, stc);
+  const double tau = stc[0];
+  const T th[3] = {T(stc[1]), T(stc[2]), T(stc[3])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   const bool first_order = (A.flags & PPML_FIRST_ORDER) != 0;
@@ -557,29 +559,48 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   T vmax = T(0), cmax = T(0);
   unsigned long long nvac = 0, nbad = 0;
   const float rho_vac_up = __double2float_ru(A.rho_vac);
-#pragma unroll 2
-  for (int c = 0; c < nvalid_z; c++) {
-    const long long idx = zline0 + g.nxy * c;
-    T u[6];
+  // groups of FB cells: all loads of a group are issued before its first store
+  constexpr int FB = 2;
+#pragma unroll 1
+  for (int c0 = 0; c0 < nvalid_z; c0 += FB) {
+    T u[FB][6];
 #pragma unroll
-    for (int f = 0; f < 6; f++) u[f] = A.out[f][idx];
-    if constexpr (sizeof(T) == 4)
-      nvac += correct_energy_f32(u, rho_vac_up, A.rho_vac);
-    else
-      nvac += correct_energy<T>(u, A.rho_vac);
-    A.out[1][idx] = u[1];
-    A.out[2][idx] = u[2];
-    A.out[3][idx] = u[3];
-    A.out[5][idx] = u[5];
-    sums.add(u);
-    if constexpr (sizeof(T) == 4)
-      cell_speeds_f32(u, gamma, gm1, vmax, cmax, nbad);
-    else
-      cell_speeds<T>(u, gamma, gm1, vmax, cmax, nbad);
+    for (int q = 0; q < FB; q++)
+      if (c0 + q < nvalid_z)
+#pragma unroll
+        for (int f = 0; f < 6; f++) u[q][f] = A.out[f][zline0 + g.nxy * (c0 + q)];
+#pragma unroll
+    for (int q = 0; q < FB; q++) {
+      if (c0 + q >= nvalid_z) break;
+      const long long idx = zline0 + g.nxy * (c0 + q);
+      if constexpr (sizeof(T) == 4)
+        nvac += correct_energy_f32(u[q], rho_vac_up, A.rho_vac);
+      else
+        nvac += correct_energy<T>(u[q], A.rho_vac);
+      A.out[1][idx] = u[q][1];
+      A.out[2][idx] = u[q][2];
+      A.out[3][idx] = u[q][3];
+      A.out[5][idx] = u[q][5];
+      sums.add(u[q]);
+      if constexpr (sizeof(T) == 4)
+        cell_speeds_f32(u[q], gamma, gm1, vmax, cmax, nbad);
+      else
+        cell_speeds<T>(u[q], gamma, gm1, vmax, cmax, nbad);
+    }
   }
-  double sd[6];
-  sums.get(sd);
-  block_reduce_store<TN>(sd, (double)vmax, (double)cmax, nvac, nbad, A.partials);
+  if constexpr (sizeof(T) == 4) {
+    float hi[6], lo[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      hi[f] = sums.s[f].hi;
+      lo[f] = sums.s[f].lo;
+    }
+    block_reduce_store_f32<TN>(hi, lo, vmax, cmax, (unsigned)nvac, (unsigned)nbad, A.partials);
+  } else {
+    double sd[6];
+    sums.get(sd);
+    block_reduce_store<TN>(sd, (double)vmax, (double)cmax, nvac, nbad, A.partials);
+  }
 }
 
 // ====================================================================== Eulerian stage
@@ -603,11 +624,15 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
-  const double tau = read_tau(A.dt_dev, A.dt_host);
-  const T th[3] = {T(tau / A.h[0]), T(tau / A.h[1]), T(tau / A.h[2])};
+  double stc[4];
+  cta_step_constants(A.dt_dev, A.dt_host, A.h, stc);
+  const double tau = stc[0];
+  const T th[3] = {T(stc[1]), T(stc[2]), T(stc[3])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
 
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
+  const long long zline0e =
+      (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
   bool first = true;
 #pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
@@ -699,6 +724,27 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   }
   __syncthreads();
   // rho E, rho eps (and the optional gravity source), cells of the thread's z line
+  if (tg.fast && !A.phi && !A.out[0]) {  // interior tile: loads of 8 cells in flight
+    constexpr int EB = 8;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TB; c0 += EB) {
+      T en[EB], ei[EB];
+#pragma unroll
+      for (int q = 0; q < EB; q++) {
+        const long long idx = zline0e + g.nxy * (c0 + q);
+        en[q] = A.u[4][idx];
+        ei[q] = A.u[5][idx];
+      }
+#pragma unroll
+      for (int q = 0; q < EB; q++) {
+        const long long idx = zline0e + g.nxy * (c0 + q);
+        const int ai = acc_at(a, b, c0 + q);
+        A.out[4][idx] = en[q] - S.apv[ai];
+        A.out[5][idx] = ei[q] - gm1 * ei[q] * S.av[ai];
+      }
+    }
+    return;
+  }
   for (int c = 0; c < TB; c++) {
     if (!in_domain(g, tg, a, b, c)) continue;
     const int gi = tg.i0 + a, gj = tg.j0 + b, gk = tg.k0 + c;
