@@ -52,21 +52,39 @@ __device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, int tiles_x, in
   return t;
 }
 
-// Linear index of tile-relative cell (i, j, k) and the mirror flags of its mapping.
-__device__ __forceinline__ long long cell_index(const GridGeom& g, const TileGeom& t, int i, int j,
-                                                int k, int& flips) {
-  if (t.fast) {
-    flips = 0;
-    return (long long)(t.i0 + i) + (long long)g.n[0] * (t.j0 + j) + g.nxy * (t.k0 + k);
+// Per-axis maps of the tile-relative coordinates -TH .. TB + TH - 1 to global offsets (the
+// boundary-mapped coordinate times the axis stride, bc_map) and mirror flags (bit a for
+// axis a), built once per CTA; a cell's offset is the sum of its three axis offsets and
+// its flags the OR of the axis flags, which is map_cell without per-element arithmetic.
+struct TileMaps {
+  long long off[3][TW];
+  int flip[3][TW];
+};
+
+__device__ __forceinline__ void build_maps(TileMaps& M, const GridGeom& g, const TileGeom& t) {
+  for (int e = threadIdx.x; e < 3 * TW; e += blockDim.x) {
+    const int ax = e / TW, c = e % TW - TH;
+    const int o = ax == 0 ? t.i0 : (ax == 1 ? t.j0 : t.k0);
+    int fl;
+    const int m = bc_map(o + c, g.n[ax], g.bc[2 * ax], g.bc[2 * ax + 1], fl);
+    const long long stride = ax == 0 ? 1LL : (ax == 1 ? (long long)g.n[0] : g.nxy);
+    M.off[ax][c + TH] = (long long)m * stride;
+    M.flip[ax][c + TH] = fl << ax;
   }
-  return map_cell(t.i0 + i, t.j0 + j, t.k0 + k, g, flips);
 }
 
+__device__ __forceinline__ long long map_off(const TileMaps& M, int i, int j, int k, int& fl) {
+  fl = M.flip[0][i + TH] | M.flip[1][j + TH] | M.flip[2][k + TH];
+  return M.off[0][i + TH] + M.off[1][j + TH] + M.off[2][k + TH];
+}
+
+// Field f at tile-relative cell (i, j, k) through the maps (momentum normal to a
+// reflecting wall negated).
 template <typename T>
-__device__ __forceinline__ T load_field(const T* __restrict__ q, int f, const GridGeom& g,
-                                        const TileGeom& t, int i, int j, int k) {
+__device__ __forceinline__ T load_mapped(const T* __restrict__ q, int f, const TileMaps& M, int i,
+                                         int j, int k) {
   int fl;
-  const T v = q[cell_index(g, t, i, j, k, fl)];
+  const T v = q[map_off(M, i, j, k, fl)];
   return field_flipped(f, fl) ? -v : v;
 }
 
@@ -247,6 +265,36 @@ __device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, co
   return (i + 1) + 18 * (j + 1) + 324 * (k + 1);
 }
 
+// One field over the dense 18^3 box (tile coordinates -1..16) of any tile, through the
+// tile maps: asynchronous copies when async, else loads with the sign of component
+// `flip_axis` of the momentum negated where that axis was mirrored (-1: no flip).
+template <typename T>
+__device__ __forceinline__ void stage_box_maps(T* box, const T* __restrict__ src,
+                                               const TileMaps& M, int tid, int flip_axis,
+                                               bool async) {
+  int i = tid % 18, j = (tid / 18) % 18, k = tid / 324;
+  for (int it = tid; it < 18 * 18 * 18; it += TN) {
+    int fl;
+    const long long o = map_off(M, i - 1, j - 1, k - 1, fl);
+    if (async) {
+      cp_async_elem(&box[it], src + o);
+    } else {
+      const T v = src[o];
+      box[it] = (flip_axis >= 0 && ((fl >> flip_axis) & 1)) ? -v : v;
+    }
+    i += 4;
+    if (i >= 18) {
+      i -= 18;
+      j++;
+    }
+    j += 14;
+    if (j >= 18) {
+      j -= 18;
+      k++;
+    }
+  }
+}
+
 // Asynchronous copy of one field over the dense 18^3 box (tile coordinates -1..16) of an
 // interior tile: thread tid copies elements tid, tid + 256, ...; the box coordinates and
 // the global offset advance by 256 = 14 * 18 + 4 elements per copy with carries.
@@ -359,6 +407,8 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  __shared__ TileMaps maps;
+  if (!tg.fast || A.any_reflect) build_maps(maps, g, tg);  // ordered by the barrier below
   double stc[4];
   cta_step_constants(A.dt_dev, A.dt_host, A.h, stc);
   const double tau = stc[0];
@@ -381,29 +431,19 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   T* mbox = smem_t + 5832;  // m_a, then v_a
   static_assert(2 * 5832 <= LAG_FIELD + ACC, "template boxes must fit in fld + acc");
   const bool fast_async = async_ok && tg.fast;
-  if (fast_async) {
-    stage_box_fast(rbox, A.u[0], g, tg, tid);  // rho once for all three axes
-  } else {
-    for (int it = tid; it < 18 * 18 * 18; it += TN) {
-      const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
-      int fl;
-      rbox[it] = A.u[0][cell_index(g, tg, i, j, k, fl)];
-    }
-  }
+  // rho once for all three axes (never sign-flipped: always asynchronous)
+  if (fast_async)
+    stage_box_fast(rbox, A.u[0], g, tg, tid);
+  else
+    stage_box_maps(rbox, A.u[0], maps, tid, -1, true);
 #pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
-    if (fast_async) {
+    if (fast_async)
       stage_box_fast(mbox, A.u[1 + ax], g, tg, tid);
-    } else {
-      for (int it = tid; it < 18 * 18 * 18; it += TN) {
-        const int i = it % 18 - 1, j = (it / 18) % 18 - 1, k = it / 324 - 1;
-        int fl;
-        const T m = A.u[1 + ax][cell_index(g, tg, i, j, k, fl)];
-        mbox[it] = ((fl >> ax) & 1) ? -m : m;
-      }
-    }
-    if (fast_async) cp_async_wait_all();
+    else
+      stage_box_maps(mbox, A.u[1 + ax], maps, tid, ax, async_ok);
+    cp_async_wait_all();
     __syncthreads();
     for (int it = tid; it < 18 * 18 * 18; it += TN) {
       if constexpr (sizeof(T) == 4)
@@ -475,30 +515,34 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       }
       cp_async_commit();
     } else {
-      for (int it = tid; it < TB * TB * TB; it += TN) {  // core
-        const int i = it % TB, j = (it / TB) % TB, k = it / TN;
-        int fl;
-        const long long c = cell_index(g, tg, i, j, k, fl);
-        T* d = &S.fld[acc_at(i, j, k)];
-        if (async_ok)
-          cp_async_elem(d, src + c);
-        else
-          *d = load_field(src, f, g, tg, i, j, k);
+      // boundary tile, through the tile maps: the z column (a, b, *) of the core and the
+      // halo positions of the thread's lines on active axes
+#pragma unroll 4
+      for (int s = 0; s < TB; s++) {
+        T* d = &S.fld[acc_at(a, b, s)];
+        if (async_ok) {
+          int fl;
+          cp_async_elem(d, src + map_off(maps, a, b, s, fl));
+        } else {
+          *d = load_mapped(src, f, maps, a, b, s);
+        }
       }
-      for (int it = tid; it < 3 * HALO_POS * TN; it += TN) {  // halo positions, active axes
-        const int ax = it / (HALO_POS * TN), r = it % (HALO_POS * TN);
+#pragma unroll 1
+      for (int ax = 0; ax < 3; ax++) {
         if (!act[ax]) continue;
-        const int h = r / TN, line = r % TN;
-        const int p = h < 3 ? h - 3 : TB + h - 3;
-        int i, j, k;
-        line_cell(ax, p, line % TB, line / TB, i, j, k);
-        int fl;
-        const long long c = cell_index(g, tg, i, j, k, fl);
-        T* d = &S.fld[halo_at(ax, h, line)];
-        if (async_ok)
-          cp_async_elem(d, src + c);
-        else
-          *d = load_field(src, f, g, tg, i, j, k);
+#pragma unroll
+        for (int h = 0; h < HALO_POS; h++) {
+          const int p = h < 3 ? h - 3 : TB + h - 3;
+          int i, j, k;
+          line_cell(ax, p, a, b, i, j, k);
+          T* d = &S.fld[halo_at(ax, h, tid)];
+          if (async_ok) {
+            int fl;
+            cp_async_elem(d, src + map_off(maps, i, j, k, fl));
+          } else {
+            *d = load_mapped(src, f, maps, i, j, k);
+          }
+        }
       }
     }
     if (async_ok && !fast_async) cp_async_wait_all();
@@ -624,6 +668,8 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  __shared__ TileMaps maps;
+  build_maps(maps, g, tg);  // ordered by the barrier below
   double stc[4];
   cta_step_constants(A.dt_dev, A.dt_host, A.h, stc);
   const double tau = stc[0];
@@ -669,7 +715,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       int i, j, k;
       line_cell(ax, p, s % TB, s / TB, i, j, k);
       int fl;
-      const long long c = cell_index(g, tg, i, j, k, fl);
+      const long long c = map_off(maps, i, j, k, fl);
       const int o = slab_at(p, s % TB, s / TB);
       if (async_ok) {
         cp_async_elem(&S.r[o], A.u[0] + c);
