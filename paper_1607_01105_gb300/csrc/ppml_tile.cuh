@@ -399,6 +399,40 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
   for (int c = TB - 3; c < TB; c++) step(halo[(c - TB + 6) * SLP], c);
 }
 
+// Face velocities v^ of line (a, b) along axis ax (faces 0..16, face c between cells c-1
+// and c) from the dense 18^3 boxes of v_ax and rho: the 9-point template in the plane normal
+// to ax (eq. veltemplate; the cell's own v in the one-point variant) and the sqrt(rho)
+// weighted average of the two adjacent cells (eq. modspaceaveragevelocitylagrange).
+template <typename T>
+__device__ __forceinline__ void line_face_velocities(const T* vb, const T* rb, int ax, int a,
+                                                     int b, bool one_point, T out[TB + 1]) {
+  // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
+  const int s_ax = ax == 0 ? 1 : (ax == 1 ? 18 : 324);
+  const int s_b = ax == 0 ? 18 : (ax == 1 ? 324 : 1);
+  const int s_c = ax == 0 ? 324 : (ax == 1 ? 1 : 18);
+  int li, lj, lk;
+  line_cell(ax, 0, a, b, li, lj, lk);
+  const int base = tbox_at(li, lj, lk);
+  T vt_prev = T(0), sq_prev = T(0);
+#pragma unroll
+  for (int p = -1; p <= TB; p++) {
+    const int o = base + p * s_ax;
+    const T corners = vb[o + s_b + s_c] + vb[o + s_b - s_c] + vb[o - s_b + s_c] + vb[o - s_b - s_c];
+    const T edges = vb[o + s_b] + vb[o - s_b] + vb[o + s_c] + vb[o - s_c];
+    const T vt = one_point ? vb[o] : corners / T(16) + edges / T(8) + vb[o] / T(4);
+    T sq;
+    if constexpr (sizeof(T) == 4) {
+      sq = sqrt_approx(rb[o]);
+      if (p >= 0) out[p] = (vt * sq + vt_prev * sq_prev) * rcp_approx(sq + sq_prev);
+    } else {
+      sq = sqrt(rb[o]);
+      if (p >= 0) out[p] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
+    }
+    vt_prev = vt;
+    sq_prev = sq;
+  }
+}
+
 template <typename T, int MINB>
 __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -423,15 +457,20 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
 
   // ---- face velocities of every line (eqs. veltemplate, modspaceaveragevelocitylagrange)
-  // rho and m_a over [-1, 16]^3 are staged in the field + accumulator space (free until the
-  // field loop), v_a = m_a / rho is formed in place, then each line forms its face
-  // velocities.
+  // rho and the three momenta over [-1, 16]^3 are staged at once -- rho and m_x in the
+  // field + accumulator space, m_y and m_z in the face-velocity space, free until written --
+  // and turned into velocities in place.  The y and z lines keep their face velocities in
+  // registers until every thread has read the y and z boxes; then the x lines write theirs
+  // and all three sets are stored.
   T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
-  T* rbox = smem_t;         // rho, dense 18^3
-  T* mbox = smem_t + 5832;  // m_a, then v_a
+  T* rbox = smem_t;                                  // rho, dense 18^3
+  T* const vspace = &S.vh[0][0][0];
+  // m_a, then v_a
+  auto vbox = [&](int ax) { return ax == 0 ? smem_t + 5832 : vspace + (ax - 1) * 5832; };
   static_assert(2 * 5832 <= LAG_FIELD + ACC, "template boxes must fit in fld + acc");
+  static_assert(2 * 5832 <= 3 * (TB + 1) * TN, "two boxes must fit in the face-velocity space");
   const bool fast_async = async_ok && tg.fast;
-  // rho once for all three axes (never sign-flipped: always asynchronous)
+  // rho never changes sign: always asynchronous
   if (fast_async)
     stage_box_fast(rbox, A.u[0], g, tg, tid);
   else
@@ -440,47 +479,42 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
     if (fast_async)
-      stage_box_fast(mbox, A.u[1 + ax], g, tg, tid);
+      stage_box_fast(vbox(ax), A.u[1 + ax], g, tg, tid);
     else
-      stage_box_maps(mbox, A.u[1 + ax], maps, tid, ax, async_ok);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int it = tid; it < 18 * 18 * 18; it += TN) {
-      if constexpr (sizeof(T) == 4)
-        mbox[it] = mbox[it] * rcp_approx(rbox[it]);
-      else
-        mbox[it] = mbox[it] / rbox[it];
-    }
-    __syncthreads();
-    // transverse roles of eq. veltemplate: axis x -> (y, z), y -> (z, x), z -> (x, y)
-    const int s_ax = ax == 0 ? 1 : (ax == 1 ? 18 : 324);
-    const int s_b = ax == 0 ? 18 : (ax == 1 ? 324 : 1);
-    const int s_c = ax == 0 ? 324 : (ax == 1 ? 1 : 18);
-    int li, lj, lk;
-    line_cell(ax, 0, a, b, li, lj, lk);
-    const int base = tbox_at(li, lj, lk);
-    T vt_prev = T(0), sq_prev = T(0);
-#pragma unroll 2
-    for (int p = -1; p <= TB; p++) {
-      const int o = base + p * s_ax;
-      const T corners = mbox[o + s_b + s_c] + mbox[o + s_b - s_c] + mbox[o - s_b + s_c] +
-                        mbox[o - s_b - s_c];
-      const T edges = mbox[o + s_b] + mbox[o - s_b] + mbox[o + s_c] + mbox[o - s_c];
-      const T vt = one_point ? mbox[o] : corners / T(16) + edges / T(8) + mbox[o] / T(4);
-      if constexpr (sizeof(T) == 4) {
-        const float sq = sqrt_approx(rbox[o]);
-        if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) * rcp_approx(sq + sq_prev);
-        vt_prev = vt;
-        sq_prev = sq;
-        continue;
-      }
-      const T sq = sqrt(rbox[o]);
-      if (p >= 0) S.vh[ax][p][tid] = (vt * sq + vt_prev * sq_prev) / (sq + sq_prev);
-      vt_prev = vt;
-      sq_prev = sq;
-    }
-    __syncthreads();
+      stage_box_maps(vbox(ax), A.u[1 + ax], maps, tid, ax, async_ok);
   }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int it = tid; it < 18 * 18 * 18; it += TN) {
+    const T r = rbox[it];
+    if constexpr (sizeof(T) == 4) {
+      const float ir = rcp_approx(r);
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++)
+        if (act[ax]) vbox(ax)[it] = vbox(ax)[it] * ir;
+    } else {
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++)
+        if (act[ax]) vbox(ax)[it] = vbox(ax)[it] / r;
+    }
+  }
+  __syncthreads();
+  T vh1[TB + 1], vh2[TB + 1];
+  if (act[1]) line_face_velocities(vbox(1), rbox, 1, a, b, one_point, vh1);
+  if (act[2]) line_face_velocities(vbox(2), rbox, 2, a, b, one_point, vh2);
+  __syncthreads();  // the y and z boxes are read; the face-velocity space is free
+  if (act[0]) {
+    T vh0[TB + 1];
+    line_face_velocities(vbox(0), rbox, 0, a, b, one_point, vh0);
+#pragma unroll
+    for (int q = 0; q <= TB; q++) S.vh[0][q][tid] = vh0[q];
+  }
+#pragma unroll
+  for (int q = 0; q <= TB; q++) {
+    if (act[1]) S.vh[1][q][tid] = vh1[q];
+    if (act[2]) S.vh[2][q][tid] = vh2[q];
+  }
+  __syncthreads();
 
   // ---- per field: stage, sweep x, y (into acc), z (finish into the output)
 #pragma unroll 1
@@ -529,34 +563,37 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       }
 #pragma unroll 1
       for (int ax = 0; ax < 3; ax++) {
-        if (!act[ax]) continue;
+        if (act[ax]) {
 #pragma unroll
-        for (int h = 0; h < HALO_POS; h++) {
-          const int p = h < 3 ? h - 3 : TB + h - 3;
-          int i, j, k;
-          line_cell(ax, p, a, b, i, j, k);
-          T* d = &S.fld[halo_at(ax, h, tid)];
-          if (async_ok) {
-            int fl;
-            cp_async_elem(d, src + map_off(maps, i, j, k, fl));
-          } else {
-            *d = load_mapped(src, f, maps, i, j, k);
+          for (int h = 0; h < HALO_POS; h++) {
+            const int p = h < 3 ? h - 3 : TB + h - 3;
+            int i, j, k;
+            line_cell(ax, p, a, b, i, j, k);
+            T* d = &S.fld[halo_at(ax, h, tid)];
+            if (async_ok) {
+              int fl;
+              cp_async_elem(d, src + map_off(maps, i, j, k, fl));
+            } else {
+              *d = load_mapped(src, f, maps, i, j, k);
+            }
           }
         }
+        if (async_ok) cp_async_commit();  // same three groups as on interior tiles
       }
     }
-    if (async_ok && !fast_async) cp_async_wait_all();
-    if (fast_async) cp_async_wait_group<2>();  // core and x halo
+    // three commit groups when asynchronous: core + x halo, y halo, z halo; each sweep
+    // waits only for the group it reads, so the later copies overlap the earlier sweeps
+    if (async_ok) cp_async_wait_group<2>();
     __syncthreads();
     int mode = 0;
 #pragma unroll 1
     for (int ax = 0; ax < 3; ax++) {
       if (!act[ax]) continue;
-      if (fast_async && ax == 1) {  // y halo (the barrier after the x sweep orders it)
+      if (async_ok && ax == 1) {  // y halo (the barrier after the x sweep orders it)
         cp_async_wait_group<1>();
         __syncthreads();
       }
-      if (fast_async && ax == 2) {
+      if (async_ok && ax == 2) {
         cp_async_wait_group<0>();
         __syncthreads();
       }
