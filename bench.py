@@ -221,6 +221,8 @@ def main():
     bb = inputs.batched_riemann(max_speed=exact.riemann_max_speed)
     bst = [torch.as_tensor(x).to(dev, torch.float32) for x in bb.u]
     batch = ppml.Batch(bb.ncells, bb.h, bb.t_end, bb.gamma, bb.cfl, ppml.PPML_F32)
+    # CTA size per instance picked by the library's autotuner (untimed; scratch copies)
+    b_threads, b_tune = batch.tune(bst, trial_steps=20, stream=stream)
     barrier()
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
@@ -233,7 +235,8 @@ def main():
     batch_updates = float(np.dot(bb.ncells.astype(np.float64), np.asarray(bt_steps, dtype=np.float64)))
     results["batch"] = {"ms": max_over_ranks_(bms), "updates": batch_updates,
                         "instances": int(bb.ncells.size), "cells": int(bb.cells),
-                        "done": int(sum(1 for t, te in zip(bt_t, bb.t_end) if t >= te))}
+                        "done": int(sum(1 for t, te in zip(bt_t, bb.t_end) if t >= te)),
+                        "threads": b_threads, "tune_ms": {str(k): v for k, v in b_tune.items()}}
     batch.close()
     del bst
     for dtype, name in ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64")):
@@ -339,6 +342,8 @@ def main():
                               "instances": results["batch"]["instances"],
                               "cells": results["batch"]["cells"],
                               "finished": results["batch"]["done"], "dtype": "f32",
+                              "cta_threads": results["batch"]["threads"],
+                              "tune_ms_20_steps": results["batch"]["tune_ms"],
                               "workload": "512 uneven 1D Riemann problems (128..4096 cells), "
                                           "each run to its own end time in one persistent launch"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",

@@ -236,6 +236,19 @@ int ppml_batch_init(int n_inst, const int* ncells, const double* h, const double
 int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* done_host,
                     void* stream);
 
+/* Launch shape of the batch (the paper has no counterpart: a systems choice).  Each
+ * instance is one CTA of 256, 512 or 1024 threads; ppml_batch_init selects 512.
+ * ppml_batch_set_threads fixes the size (PPML_E_INVAL for any other value).
+ * ppml_batch_tune times each size for trial_steps steps (>= 1) of the given state, the
+ * fastest of two runs each, on scratch copies of the state and of the instances' times
+ * (the caller's state and the batch's progress are unchanged), keeps the fastest and
+ * returns it in *threads_out (may be NULL) and the three times in ms_out[3] (may be NULL).
+ * Allocates and frees scratch of one state; synchronizes the stream.  Results of a step
+ * do not depend on the size in FP64 (the same operations per cell in the same order). */
+int ppml_batch_set_threads(ppml_batch* b, int threads);
+int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps, int* threads_out,
+                    double ms_out[3], void* stream);
+
 /* Per-instance time reached and steps taken (host arrays of n_inst).  Synchronizes. */
 int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream);
 

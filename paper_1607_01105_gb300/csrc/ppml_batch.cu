@@ -22,7 +22,32 @@ struct ppml_batch {
   InstDev* inst;
   int* order;
   size_t smem;
+  int threads;  // CTA size of the launch: 256, 512 or 1024 (ppml_batch_tune / _set_threads)
 };
+
+namespace {
+constexpr int kBatchSizes[3] = {256, 512, 1024};
+
+int launch_typed(ppml_batch* b, void* const state[4], InstDev* inst, int max_steps, int threads,
+                 cudaStream_t st) {
+  return b->dtype == PPML_F64
+             ? launch_batch<double>((double*)state[0], (double*)state[1], (double*)state[2],
+                                    (double*)state[3], inst, b->order, b->gamma, b->cfl,
+                                    max_steps, b->nmax, b->n_inst, b->smem, threads, st)
+             : launch_batch<float>((float*)state[0], (float*)state[1], (float*)state[2],
+                                   (float*)state[3], inst, b->order, b->gamma, b->cfl, max_steps,
+                                   b->nmax, b->n_inst, b->smem, threads, st);
+}
+
+int check_state(void* const state[4]) {
+  if (!state) return ppml_fail(PPML_E_INVAL, "state is NULL");
+  for (int f = 0; f < 4; f++) {
+    if (!state[f]) return ppml_fail(PPML_E_INVAL, "state field %d is NULL", f);
+    if (((uintptr_t)state[f]) & 15u) return ppml_fail(PPML_E_INVAL, "state field %d misaligned", f);
+  }
+  return PPML_OK;
+}
+}  // namespace
 
 extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
                                const double* t_end, double gamma, double cfl,
@@ -76,6 +101,7 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
   b->gamma = gamma;
   b->cfl = cfl;
   b->smem = smem;
+  b->threads = 512;
   if (cudaMalloc(&b->inst, sizeof(InstDev) * n_inst) != cudaSuccess ||
       cudaMalloc(&b->order, sizeof(int) * n_inst) != cudaSuccess) {
     ppml_batch_free(b);
@@ -93,20 +119,12 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
 extern "C" int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* done_host,
                                void* stream) {
   ppml_clear_error();
-  if (!b || !state) return ppml_fail(PPML_E_INVAL, "batch or state is NULL");
-  for (int f = 0; f < 4; f++) {
-    if (!state[f]) return ppml_fail(PPML_E_INVAL, "state field %d is NULL", f);
-    if (((uintptr_t)state[f]) & 15u) return ppml_fail(PPML_E_INVAL, "state field %d misaligned", f);
-  }
+  if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
+  int rc = check_state(state);
+  if (rc) return rc;
   if (max_steps < 0) return ppml_fail(PPML_E_INVAL, "max_steps < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = b->dtype == PPML_F64
-               ? launch_batch<double>((double*)state[0], (double*)state[1], (double*)state[2],
-                                      (double*)state[3], b->inst, b->order, b->gamma, b->cfl,
-                                      max_steps, b->nmax, b->n_inst, b->smem, st)
-               : launch_batch<float>((float*)state[0], (float*)state[1], (float*)state[2],
-                                     (float*)state[3], b->inst, b->order, b->gamma, b->cfl,
-                                     max_steps, b->nmax, b->n_inst, b->smem, st);
+  rc = launch_typed(b, state, b->inst, max_steps, b->threads, st);
   if (rc) return rc;
   if (done_host) {
     std::vector<InstDev> hi(b->n_inst);
@@ -118,6 +136,79 @@ extern "C" int ppml_batch_step(ppml_batch* b, void* const state[4], int max_step
     for (auto& x : hi) d += x.done;
     *done_host = d;
   }
+  return PPML_OK;
+}
+
+extern "C" int ppml_batch_set_threads(ppml_batch* b, int threads) {
+  ppml_clear_error();
+  if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
+  for (int s : kBatchSizes)
+    if (s == threads) {
+      b->threads = threads;
+      return PPML_OK;
+    }
+  return ppml_fail(PPML_E_INVAL, "threads = %d is not 256, 512 or 1024", threads);
+}
+
+extern "C" int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps,
+                               int* threads_out, double ms_out[3], void* stream) {
+  ppml_clear_error();
+  if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
+  int rc = check_state(state);
+  if (rc) return rc;
+  if (trial_steps < 1) return ppml_fail(PPML_E_INVAL, "trial_steps = %d must be >= 1", trial_steps);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t elt = b->dtype == PPML_F64 ? 8 : 4;
+  // scratch copies: the trials advance these, never the caller's state or the batch's times
+  void* scratch[4] = {nullptr, nullptr, nullptr, nullptr};
+  InstDev* inst = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best_ms = 0.0;
+  int best = b->threads;
+  rc = PPML_OK;
+  for (int f = 0; f < 4 && rc == PPML_OK; f++)
+    if (cudaMalloc(&scratch[f], elt * (size_t)b->total) != cudaSuccess)
+      rc = ppml_fail(PPML_E_NOMEM, "tuning scratch state");
+  if (rc == PPML_OK && cudaMalloc(&inst, sizeof(InstDev) * b->n_inst) != cudaSuccess)
+    rc = ppml_fail(PPML_E_NOMEM, "tuning scratch metadata");
+  if (rc == PPML_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = ppml_fail(PPML_E_CUDA, "cudaEventCreate failed");
+  for (int k = 0; k < 3 && rc == PPML_OK; k++) {
+    const int threads = kBatchSizes[k];
+    float best_k = 0.f;
+    for (int rep = 0; rep < 2 && rc == PPML_OK; rep++) {  // the first repetition also warms up
+      for (int f = 0; f < 4; f++)
+        if (cudaMemcpyAsync(scratch[f], state[f], elt * (size_t)b->total, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+          rc = ppml_fail(PPML_E_CUDA, "tuning copy: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rc == PPML_OK && cudaMemcpyAsync(inst, b->inst, sizeof(InstDev) * b->n_inst,
+                                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = ppml_fail(PPML_E_CUDA, "tuning copy: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      rc = launch_typed(b, scratch, inst, trial_steps, threads, st);
+      if (rc) break;
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = ppml_fail(PPML_E_CUDA, "tuning timing: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rep == 0 || ms < best_k) best_k = ms;
+    }
+    if (rc) break;
+    if (ms_out) ms_out[k] = best_k;
+    if (k == 0 || best_k < best_ms) {
+      best_ms = best_k;
+      best = threads;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int f = 0; f < 4; f++)
+    if (scratch[f]) cudaFree(scratch[f]);
+  if (inst) cudaFree(inst);
+  if (rc) return rc;
+  b->threads = best;
+  if (threads_out) *threads_out = best;
   return PPML_OK;
 }
 

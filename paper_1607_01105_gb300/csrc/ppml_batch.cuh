@@ -5,13 +5,14 @@
 // the 1D case of Sec. 1: Eulerian face solve, upwind Lagrangian fluxes, energy
 // correction of Sec. 1.4.  In 1D the 9-point template (eq. veltemplate) runs on the cell
 // itself (its transverse neighbours are the cell), evaluated term by term.  Outflow
-// boundaries on both ends.  CTAs never wait on one another.
+// boundaries on both ends.  CTAs never wait on one another.  The CTA size (threads per
+// instance) is a template parameter; the host picks it by timing the candidates on the
+// actual batch (ppml_batch_tune).
 #pragma once
 #include "ppml_device.cuh"
 
 namespace ppml {
 
-constexpr int kBatchThreads = 512;
 constexpr int kBatchGhost = 3;
 
 struct InstDev {
@@ -52,6 +53,15 @@ __device__ __forceinline__ T template_1d(T v) {
   return four / T(16) + four / T(8) + v / T(4);
 }
 
+// v = m / rho: approximate reciprocal in FP32 (as in the stage kernels), IEEE in FP64.
+template <typename T>
+__device__ __forceinline__ T vel_of(T m, T r) {
+  if constexpr (sizeof(T) == 4)
+    return m * rcp_approx(r);
+  else
+    return m / r;
+}
+
 __device__ __forceinline__ double block_max_sum(double a, double b, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -78,8 +88,31 @@ __device__ __forceinline__ double block_max_sum(double a, double b, double* sh) 
   return r;
 }
 
+// Vacuum threshold of every instance (Sec. 1.4: a fraction of the mean density; the
+// fraction is stored negated until this kernel has run): the instance's mean initial
+// density from a fixed 256-thread reduction, so the threshold does not depend on the CTA
+// size of the stepping kernel.
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(T* __restrict__ g_rho,
+__global__ void __launch_bounds__(256) batch_vacuum_kernel(const T* __restrict__ g_rho,
+                                                          InstDev* __restrict__ inst) {
+  __shared__ double red[8];
+  InstDev& I = inst[blockIdx.x];
+  if (I.rho_vac >= 0.0) return;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < I.n; c += 256) s += (double)g_rho[I.off + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    for (int q = 0; q < 8; q++) S += red[q];
+    I.rho_vac = -I.rho_vac * (S / I.n);
+  }
+}
+
+template <typename T, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rho,
                                                               T* __restrict__ g_m,
                                                               T* __restrict__ g_en,
                                                               T* __restrict__ g_ei,
@@ -109,32 +142,22 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(T* __restrict__
   }
   __syncthreads();
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
-  if (I.steps == 0 && I.rho_vac < 0.0) {
-    // vacuum threshold reference: the instance's mean initial density
-    double s = 0.0;
-    for (int c = tid; c < n; c += blockDim.x) s += (double)R[c + kBatchGhost];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((tid & 31) == 0) red[tid >> 5] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double S = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); q++) S += red[q];
-      red[79] = S / n;
-    }
-    __syncthreads();
-    I.rho_vac = -I.rho_vac * red[79];  // stored as the negated fraction before the first call
-    __syncthreads();
-  }
   for (int s = 0; s < max_steps; s++) {
     // CFL step of the current state (Sec. 1.1), per cell in the checker's order
     double vm = 0.0, cm = 0.0;
     for (int c = tid; c < n; c += blockDim.x) {
       const T r = R[c + kBatchGhost];
-      const T vx = M[c + kBatchGhost] / r, vy = T(0) / r, vz = T(0) / r;
-      const T v = sqrt(vx * vx + vy * vy + vz * vz);
       const T p = gm1 * Ei[c + kBatchGhost];
-      const T cs = sqrt(gamma * p / r);
+      T v, cs;
+      if constexpr (sizeof(T) == 4) {
+        const float ir = rcp_approx(r);
+        v = fabsf(M[c + kBatchGhost] * ir);
+        cs = sqrt_approx(gamma * p * ir);
+      } else {
+        const T vx = M[c + kBatchGhost] / r, vy = T(0) / r, vz = T(0) / r;
+        v = sqrt(vx * vx + vy * vy + vz * vz);
+        cs = sqrt(gamma * p / r);
+      }
       vm = fmax(vm, (double)v);
       cm = fmax(cm, (double)cs);
     }
@@ -156,18 +179,30 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(T* __restrict__
       T v[6], p[6];
 #pragma unroll
       for (int q = 0; q < 6; q++) {
-        v[q] = M[f + q] / R[f + q];
+        v[q] = vel_of(M[f + q], R[f + q]);
         p[q] = gm1 * Ei[f + q];
       }
       Parab<T> vL, vR, pL, pR;
       pair_parabolas(v, vL, vR);
       pair_parabolas(p, pL, pR);
-      T lam, Z;
-      face_constants(R[f + 2], R[f + 3], p[2], p[3], gamma, lam, Z);
-      const T y = Prec<T>::courant(lam, dt, I.h, th);
       T V, P;
-      riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
-                 avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
+      if constexpr (sizeof(T) == 4) {
+        const float rl = R[f + 2], rr = R[f + 3];
+        float lam, Z, hrz;
+        face_constants_f32(rl, rr, sqrt_approx(rl), sqrt_approx(rr), p[2], p[3], gamma, lam, Z,
+                           hrz);
+        const float y = lam * th;
+        const float vls = avg_right(vL.R, vL.D, vL.S, y), vrs = avg_left(vR.L, vR.D, vR.S, y);
+        const float pls = avg_right(pL.R, pL.D, pL.S, y), prs = avg_left(pR.L, pR.D, pR.S, y);
+        V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
+        P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
+      } else {
+        T lam, Z;
+        face_constants(R[f + 2], R[f + 3], p[2], p[3], gamma, lam, Z);
+        const T y = Prec<T>::courant(lam, dt, I.h, th);
+        riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
+                   avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
+      }
       FA[f] = V;
       FB[f] = P;
     }
@@ -188,9 +223,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(T* __restrict__
     // Lagrangian stage: v hat at faces, then each field's flux and update
     for (int f = tid; f <= n; f += blockDim.x) {
       const T rl = R[f + 2], rr = R[f + 3];
-      const T sl = sqrt(rl), sr = sqrt(rr);
-      const T vtl = template_1d(M[f + 2] / rl), vtr = template_1d(M[f + 3] / rr);
-      FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
+      const T vtl = template_1d(vel_of(M[f + 2], rl)), vtr = template_1d(vel_of(M[f + 3], rr));
+      if constexpr (sizeof(T) == 4) {
+        const float sl = sqrt_approx(rl), sr = sqrt_approx(rr);
+        FA[f] = (vtr * sr + vtl * sl) * rcp_approx(sr + sl);
+      } else {
+        const T sl = sqrt(rl), sr = sqrt(rr);
+        FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
+      }
     }
     __syncthreads();
     T* fields[4] = {R, M, E, Ei};

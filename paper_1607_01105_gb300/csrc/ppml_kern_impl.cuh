@@ -87,21 +87,47 @@ int launch_poisson_symbol<PPML_REAL>(void* spec, const double* tx, const double*
   return ppml_check_launch("poisson_symbol_kernel");
 }
 
-template <>
-int launch_batch<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
-                            InstDev* inst, const int* order, double gamma, double cfl,
-                            int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st) {
+namespace {
+template <int NT>
+int launch_batch_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei, InstDev* inst,
+                    const int* order, double gamma, double cfl, int max_steps, int nmax,
+                    int ninst, size_t smem, cudaStream_t st) {
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<PPML_REAL>,
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<PPML_REAL, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
       return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     configured = smem;
   }
-  batch_kernel<PPML_REAL><<<ninst, kBatchThreads, smem, st>>>(rho, m, en, ei, inst, order, gamma,
-                                                              cfl, max_steps, nmax);
+  batch_kernel<PPML_REAL, NT><<<ninst, NT, smem, st>>>(rho, m, en, ei, inst, order, gamma, cfl,
+                                                       max_steps, nmax);
   return ppml_check_launch("batch_kernel");
+}
+}  // namespace
+
+template <>
+int launch_batch<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                            InstDev* inst, const int* order, double gamma, double cfl,
+                            int max_steps, int nmax, int ninst, size_t smem, int threads,
+                            cudaStream_t st) {
+  // vacuum thresholds of instances not yet started (no-op for the others)
+  batch_vacuum_kernel<PPML_REAL><<<ninst, 256, 0, st>>>(rho, inst);
+  int rc = ppml_check_launch("batch_vacuum_kernel");
+  if (rc) return rc;
+  switch (threads) {
+    case 256:
+      return launch_batch_nt<256>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax, ninst,
+                                  smem, st);
+    case 512:
+      return launch_batch_nt<512>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax, ninst,
+                                  smem, st);
+    case 1024:
+      return launch_batch_nt<1024>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax,
+                                   ninst, smem, st);
+    default:
+      return ppml_fail(PPML_E_INVAL, "batch CTA size %d is not 256, 512 or 1024", threads);
+  }
 }
 
 }  // namespace ppml

@@ -23,7 +23,8 @@ int launch_poisson_symbol(void* spec, const double* tx, const double* ty, const 
                           int ny, int nz, double coef, cudaStream_t st);
 template <typename T>
 int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
-                 double cfl, int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st);
+                 double cfl, int max_steps, int nmax, int ninst, size_t smem, int threads,
+                 cudaStream_t st);
 
 // Deterministic reduction of per-CTA partials into the step scalars (ppml_grid.cu).
 int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
@@ -46,7 +47,7 @@ int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, doubl
   template <>                                                                                \
   int launch_batch<R>(R * rho, R * m, R * en, R * ei, InstDev * inst, const int* order,       \
                       double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem, \
-                      cudaStream_t st);
+                      int threads, cudaStream_t st);
 PPML_DECLARE_LAUNCHERS(float)
 PPML_DECLARE_LAUNCHERS(double)
 #undef PPML_DECLARE_LAUNCHERS

@@ -28,7 +28,8 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_conserved_sums", "ppml_read_diag", "ppml_dt_device", "ppml_batch_init",
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
-            "ppml_poisson_periodic", "ppml_poisson_isolated")
+            "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
+            "ppml_batch_set_threads")
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -72,6 +73,9 @@ _lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
 _lib.ppml_step_phi.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), _vp, ctypes.c_double, _vp]
 _lib.ppml_poisson_periodic.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp]
 _lib.ppml_poisson_isolated.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_uint, _vp]
+_lib.ppml_batch_tune.argtypes = [_vp, ctypes.c_void_p * 4, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double), _vp]
+_lib.ppml_batch_set_threads.argtypes = [_vp, ctypes.c_int]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -273,7 +277,7 @@ class Batch:
         _check(_lib.ppml_batch_init(n, nc, hh, te, float(gamma), float(cfl), float(vacuum_frac),
                                     self.dtype, ctypes.byref(self._h)))
 
-    def step(self, fields, max_steps, sync=False, stream=None):
+    def _ptrs(self, fields):
         if len(fields) != 4:
             raise ValueError("a batch state has four fields")
         ptrs = (ctypes.c_void_p * 4)()
@@ -281,6 +285,23 @@ class Batch:
             if not t.is_cuda or not t.is_contiguous() or t.dtype != self.tdtype or t.numel() != self.total:
                 raise ValueError(f"batch field {i} has the wrong device, layout, dtype or size")
             ptrs[i] = t.data_ptr()
+        return ptrs
+
+    def tune(self, fields, trial_steps=20, stream=None):
+        """Time the CTA sizes 256/512/1024 on scratch copies of `fields`; keep the fastest.
+        Returns (threads, {threads: ms})."""
+        ptrs = self._ptrs(fields)
+        chosen = ctypes.c_int(0)
+        ms = (ctypes.c_double * 3)()
+        _check(_lib.ppml_batch_tune(self._h, ptrs, int(trial_steps), ctypes.byref(chosen), ms,
+                                    _stream(stream)))
+        return chosen.value, dict(zip((256, 512, 1024), list(ms)))
+
+    def set_threads(self, threads):
+        _check(_lib.ppml_batch_set_threads(self._h, int(threads)))
+
+    def step(self, fields, max_steps, sync=False, stream=None):
+        ptrs = self._ptrs(fields)
         done = ctypes.c_int(-1)
         _check(_lib.ppml_batch_step(self._h, ptrs, int(max_steps), ctypes.byref(done) if sync else None,
                                     _stream(stream)))

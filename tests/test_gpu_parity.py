@@ -425,6 +425,57 @@ def test_config4_batch_matches_oracle(dtype):
     assert n_loose <= 2  # the sensitivity bound is for the rare ill-conditioned instance
 
 
+@pytest.mark.parametrize("threads", [256, 1024])
+def test_config4_batch_cta_sizes_fp64_bitwise(threads):
+    """Every CTA size of the batched launch gives the oracle's result bit for bit (FP64):
+    the per-cell operations and their order do not depend on the size."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=12, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    bt.set_threads(threads)
+    st = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    for _ in range(100):
+        if bt.step(st, 1000, sync=True) == b.ncells.size:
+            break
+    got = [x.cpu().numpy() for x in st]
+    t, steps = bt.status()
+    for i in range(b.ncells.size):
+        ref, steps_o = _batch_oracle_run(b, i)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        assert steps[i] == steps_o
+        for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+            assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
+
+
+def test_config4_batch_tune_leaves_state_and_progress():
+    """The autotuner times the three CTA sizes on scratch copies: the caller's state and
+    the instances' times are unchanged, the chosen size is one of the three and is the
+    fastest measured, and a run after tuning equals an untuned run (FP64, bitwise)."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=12, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    st = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    before = [x.clone() for x in st]
+    threads, ms = bt.tune(st, trial_steps=5)
+    assert threads in (256, 512, 1024) and all(v > 0 for v in ms.values())
+    assert ms[threads] == min(ms.values())
+    assert all(torch.equal(x, y) for x, y in zip(st, before))
+    t, steps = bt.status()
+    assert max(t) == 0.0 and max(steps) == 0
+    ref_bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    ref_st = [x.clone() for x in before]
+    for _ in range(3):
+        bt.step(st, 200)
+        ref_bt.step(ref_st, 200)
+    torch.cuda.synchronize()
+    for k, (x, y) in enumerate(zip(st, ref_st)):
+        assert bool(torch.isfinite(x).all())
+        bad = torch.nonzero(x != y).flatten()
+        assert bad.numel() == 0, (k, bad[:5].tolist(), (x - y).abs().max().item())
+    with pytest.raises(ppml.PPMLError):
+        bt.set_threads(384)
+
+
 @pytest.mark.slow
 def test_config4_full_batch_sampled_instances():
     """The full 512-instance batch (lengths 128..4096) in one persistent launch per call,
