@@ -548,37 +548,44 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
         if (act[2]) cp_async_elem(&S.fld[halo_at(2, h, tid)], col + g.nxy * p);
       }
       cp_async_commit();
-    } else {
+    } else if (async_ok) {
       // boundary tile, through the tile maps: the z column (a, b, *) of the core and the
-      // halo positions of the thread's lines on active axes
+      // halo positions of the thread's lines on active axes, in the same three commit
+      // groups as on interior tiles.  The thread's line bases (the sum of the two
+      // transverse map entries) are formed once, so each copy adds one map entry.
+      const long long bx = maps.off[0][a + TH], by = maps.off[1][b + TH];
+      const long long base_z = bx + by;  // z line (a, b): x = a, y = b
 #pragma unroll 4
-      for (int s = 0; s < TB; s++) {
-        T* d = &S.fld[acc_at(a, b, s)];
-        if (async_ok) {
-          int fl;
-          cp_async_elem(d, src + map_off(maps, a, b, s, fl));
-        } else {
-          *d = load_mapped(src, f, maps, a, b, s);
-        }
-      }
+      for (int s = 0; s < TB; s++)
+        cp_async_elem(&S.fld[acc_at(a, b, s)], src + (base_z + maps.off[2][s + TH]));
 #pragma unroll 1
       for (int ax = 0; ax < 3; ax++) {
         if (act[ax]) {
+          // line (a, b) of axis ax: x line (y = a, z = b), y line (x = a, z = b), z line
+          const long long base = ax == 0 ? maps.off[1][a + TH] + maps.off[2][b + TH]
+                                         : (ax == 1 ? bx + maps.off[2][b + TH] : base_z);
 #pragma unroll
           for (int h = 0; h < HALO_POS; h++) {
             const int p = h < 3 ? h - 3 : TB + h - 3;
-            int i, j, k;
-            line_cell(ax, p, a, b, i, j, k);
-            T* d = &S.fld[halo_at(ax, h, tid)];
-            if (async_ok) {
-              int fl;
-              cp_async_elem(d, src + map_off(maps, i, j, k, fl));
-            } else {
-              *d = load_mapped(src, f, maps, i, j, k);
-            }
+            cp_async_elem(&S.fld[halo_at(ax, h, tid)], src + (base + maps.off[ax][p + TH]));
           }
         }
-        if (async_ok) cp_async_commit();  // same three groups as on interior tiles
+        cp_async_commit();  // same three groups as on interior tiles
+      }
+    } else {
+      // reflecting walls somewhere: copies through registers with the mirror signs
+#pragma unroll 4
+      for (int s = 0; s < TB; s++) S.fld[acc_at(a, b, s)] = load_mapped(src, f, maps, a, b, s);
+#pragma unroll 1
+      for (int ax = 0; ax < 3; ax++) {
+        if (!act[ax]) continue;
+#pragma unroll
+        for (int h = 0; h < HALO_POS; h++) {
+          const int p = h < 3 ? h - 3 : TB + h - 3;
+          int i, j, k;
+          line_cell(ax, p, a, b, i, j, k);
+          S.fld[halo_at(ax, h, tid)] = load_mapped(src, f, maps, i, j, k);
+        }
       }
     }
     // three commit groups when asynchronous: core + x halo, y halo, z halo; each sweep
