@@ -441,14 +441,28 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
+  const bool fast_async = async_ok && tg.fast;
+  T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
+  T* const vspace = &S.vh[0][0][0];
+  // template boxes: rho, then m_a (turned into v_a in place)
+  T* rbox = smem_t;  // rho, dense 18^3
+  auto vbox = [&](int ax) { return ax == 0 ? smem_t + 5832 : vspace + (ax - 1) * 5832; };
+  // interior tiles issue the template copies first, so that they are in flight while the
+  // per-CTA constants are formed
+  if (fast_async) {
+    stage_box_fast(rbox, A.u[0], g, tg, tid);
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ax++)
+      if (act[ax]) stage_box_fast(vbox(ax), A.u[1 + ax], g, tg, tid);
+  }
   __shared__ TileMaps maps;
-  if (!tg.fast || A.any_reflect) build_maps(maps, g, tg);  // ordered by the barrier below
+  if (!fast_async) build_maps(maps, g, tg);  // ordered by the barrier below
   double stc[4];
   cta_step_constants(A.dt_dev, A.dt_host, A.h, stc);
   const double tau = stc[0];
   const T th[3] = {T(stc[1]), T(stc[2]), T(stc[3])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
-  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   const bool first_order = (A.flags & PPML_FIRST_ORDER) != 0;
   const bool one_point = (A.flags & PPML_VHAT_1PT) != 0;
   const bool line_ok = in_domain(g, tg, a, b, 0);
@@ -462,26 +476,14 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   // and turned into velocities in place.  The y and z lines keep their face velocities in
   // registers until every thread has read the y and z boxes; then the x lines write theirs
   // and all three sets are stored.
-  T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
-  T* rbox = smem_t;                                  // rho, dense 18^3
-  T* const vspace = &S.vh[0][0][0];
-  // m_a, then v_a
-  auto vbox = [&](int ax) { return ax == 0 ? smem_t + 5832 : vspace + (ax - 1) * 5832; };
   static_assert(2 * 5832 <= LAG_FIELD + ACC, "template boxes must fit in fld + acc");
   static_assert(2 * 5832 <= 3 * (TB + 1) * TN, "two boxes must fit in the face-velocity space");
-  const bool fast_async = async_ok && tg.fast;
-  // rho never changes sign: always asynchronous
-  if (fast_async)
-    stage_box_fast(rbox, A.u[0], g, tg, tid);
-  else
+  if (!fast_async) {
+    // boundary tiles through the maps; rho never changes sign: always asynchronous
     stage_box_maps(rbox, A.u[0], maps, tid, -1, true);
 #pragma unroll 1
-  for (int ax = 0; ax < 3; ax++) {
-    if (!act[ax]) continue;
-    if (fast_async)
-      stage_box_fast(vbox(ax), A.u[1 + ax], g, tg, tid);
-    else
-      stage_box_maps(vbox(ax), A.u[1 + ax], maps, tid, ax, async_ok);
+    for (int ax = 0; ax < 3; ax++)
+      if (act[ax]) stage_box_maps(vbox(ax), A.u[1 + ax], maps, tid, ax, async_ok);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -712,6 +714,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
   const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   __shared__ TileMaps maps;
   build_maps(maps, g, tg);  // ordered by the barrier below
   double stc[4];
@@ -720,7 +723,6 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const T th[3] = {T(stc[1]), T(stc[2]), T(stc[3])};
   const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
 
-  const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   const long long zline0e =
       (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
   bool first = true;
