@@ -288,6 +288,27 @@ def main():
             ems = max_over_ranks_(e0.elapsed_time(e1))
             results["e2e"] = {"ms": ems, "steps": e_steps,
                               "h2d": 6 * cells * elt, "d2h": 6 * cells * elt}
+            # the same step mid-run: advance (untimed, at most 4000 steps) to half the time
+            # at which the blast radius reaches 0.4, then time as many steps again
+            t_mid, adv = 0.5 * pb.t_end, 0
+            while grid.diag(raise_nonphysical=False)["t"] < t_mid and adv < 4000:
+                for _ in range(100):
+                    grid.step(u, v, 0.0)
+                    u, v = v, u
+                adv += 100
+            barrier()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(steps):
+                grid.step(u, v, 0.0)
+                u, v = v, u
+            m1.record(stream)
+            barrier()
+            dm = grid.diag(raise_nonphysical=False)
+            results["mid"] = {"ms": max_over_ranks_(m0.elapsed_time(m1)), "steps": steps,
+                              "t": dm["t"], "steps_before": args.warmup + steps + e_steps + adv,
+                              "t_end": pb.t_end}
         grid.close()
         del u, v
         torch.cuda.empty_cache()
@@ -346,6 +367,11 @@ def main():
                               "tune_ms_20_steps": results["batch"]["tune_ms"],
                               "workload": "512 uneven 1D Riemann problems (128..4096 cells), "
                                           "each run to its own end time in one persistent launch"},
+            "mid_run": {"value": whole_job_rate(cells, results["mid"]["steps"], world, results["mid"]["ms"]),
+                        "unit": "Mcell-updates/s", "ms_per_step": results["mid"]["ms"] / results["mid"]["steps"],
+                        "t": results["mid"]["t"], "t_end": results["mid"]["t_end"],
+                        "steps_before": results["mid"]["steps_before"],
+                        "note": "same FP32 step timed after advancing to about half the end time"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": 3 * r32["steps"],
