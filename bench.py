@@ -41,7 +41,7 @@ OPS_LAG = 18 * 62 + 57 + 30 + 12 + 42
 OPS_EUL = 3 * (84 + 15 + 32 + 9 + 8 + 1) + 6
 # DRAM bytes per Lagrangian launch measured by ncu (dram__bytes_read + write) on the
 # 160^3 point blast, per cell (scaled to the workload's cells); see profiles/.
-NCU_LAG_DRAM_BYTES_PER_CELL = (104.774656e6 + 63.262720e6) / 160 ** 3
+NCU_LAG_DRAM_BYTES_PER_CELL = (101.341440e6 + 62.453504e6) / 160 ** 3
 SMS, FP32_LANES = 152, 128
 
 
@@ -288,8 +288,8 @@ def main():
             ems = max_over_ranks_(e0.elapsed_time(e1))
             results["e2e"] = {"ms": ems, "steps": e_steps,
                               "h2d": 6 * cells * elt, "d2h": 6 * cells * elt}
-            # the same step mid-run: advance (untimed, at most 4000 steps) to half the time
-            # at which the blast radius reaches 0.4, then time as many steps again
+            # the same step mid-run: advance (untimed) toward half the time at which the blast
+            # radius reaches 0.4, at most 4000 steps, then time as many steps again
             t_mid, adv = 0.5 * pb.t_end, 0
             while grid.diag(raise_nonphysical=False)["t"] < t_mid and adv < 4000:
                 for _ in range(100):
@@ -371,7 +371,8 @@ def main():
                         "unit": "Mcell-updates/s", "ms_per_step": results["mid"]["ms"] / results["mid"]["steps"],
                         "t": results["mid"]["t"], "t_end": results["mid"]["t_end"],
                         "steps_before": results["mid"]["steps_before"],
-                        "note": "same FP32 step timed after advancing to about half the end time"},
+                        "note": "same FP32 step timed after advancing toward half the end time "
+                                "(at most 4000 steps; t reached is given)"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": 3 * r32["steps"],
