@@ -341,6 +341,39 @@ def test_config3_point_blast_64_fp64_run():
     compare(host(u, shape_of(pb)), ref, TOL64)
 
 
+@pytest.mark.slow
+def test_config3_point_blast_256_fp64_steps():
+    """Config 3 at full size in FP64: five steps of the 256^3 point blast with the device
+    CFL step against the oracle's steps (relative L1 within 1e-10, same step sizes)."""
+    pb = inputs.point_blast_3d(256)
+    g = oracle_grid(pb)
+    ref = pb.u
+    u = ppml.to_device(pb.u, F64)
+    v = [torch.empty_like(x) for x in u]
+    grid = gpu_grid(pb, F64, u)
+    for _ in range(5):
+        dt_o = oracle.cfl_dt(g, ref)
+        assert grid.diag()["dt_next"] == pytest.approx(dt_o, rel=1e-13)
+        ref, dgo = oracle.step(g, ref, dt_o)
+        grid.step(u, v, 0.0)
+        u, v = v, u
+    compare(host(u, shape_of(pb)), ref, TOL64)
+
+
+@pytest.mark.slow
+def test_config3_point_blast_64_fp64_full_run():
+    """Config 3 setup at 64^3 in FP64 run to its end time (blast radius 0.4, 814 steps)
+    with the device-resident step and end-time clipping, against the oracle's full run."""
+    pb = inputs.point_blast_3d(64)
+    g = oracle_grid(pb)
+    ref, t, steps_o, dgo = oracle.run(g, pb.u, pb.t_end)
+    got, d, steps = run_gpu(pb, F64)
+    assert steps == steps_o and d["t"] == pytest.approx(pb.t_end, rel=1e-14)
+    compare(got, ref, TOL64)
+    for f in (0, 4):  # mass and total energy with outflow walls the blast has not reached
+        assert d["sums"][f] == pytest.approx(dgo["sums"][f], rel=1e-12)
+
+
 # ---------------------------------------------------------------- batched 1D (cfg 4)
 
 _BATCH_CACHE = {}
