@@ -267,22 +267,49 @@ def main():
         ms = max_over_ranks_(ms)
         results[name] = {"ms": ms, "steps": steps, "kernel_ms": [x / ksteps for x in kms],
                          "clocks": cs.summary(), "elt": elt, "diag": d}
-        # end to end through host buffers (FP32 headline only): pinned H2D of the input
-        # state, the step, D2H of the new state, every step inside the timed region
+        # end to end through host buffers (FP32 headline only): every step copies its input
+        # state from pinned host memory, steps, and copies the new state back to pinned host
+        # memory, all inside the timed region.  Uploads and downloads run on their own
+        # streams with two device buffers each, so the upload of step k overlaps the step
+        # and the download of step k-1 (events order every reuse of a buffer).
         if dtype == ppml.PPML_F32:
             hin = [x.cpu().pin_memory() for x in u]
-            hout = [torch.empty_like(x) for x in hin]
-            e_steps = max(3, steps // 5)
+            hout = [[torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in hin]
+                    for _ in range(2)]
+            dev_in = [u, [torch.empty_like(x) for x in u]]
+            dev_out = [v, [torch.empty_like(x) for x in u]]
+            s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+            ev_up = [torch.cuda.Event() for _ in range(2)]
+            ev_step = [torch.cuda.Event() for _ in range(2)]
+            ev_down = [torch.cuda.Event() for _ in range(2)]
+            e_steps = max(6, steps // 2)
+            torch.cuda.synchronize()
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(e_steps):
-                for dst, src in zip(u, hin):
-                    dst.copy_(src, non_blocking=True)
-                grid.step(u, v, 0.0)
-                for dst, src in zip(hout, v):
-                    dst.copy_(src, non_blocking=True)
+            s_up.wait_stream(stream)
+            s_down.wait_stream(stream)
+            for k in range(e_steps):
+                i = k % 2
+                if k >= 2:
+                    s_up.wait_event(ev_step[i])  # step k-2 has read dev_in[i]
+                with torch.cuda.stream(s_up):
+                    for dst, src in zip(dev_in[i], hin):
+                        dst.copy_(src, non_blocking=True)
+                ev_up[i].record(s_up)
+                stream.wait_event(ev_up[i])
+                if k >= 2:
+                    stream.wait_event(ev_down[i])  # step k-2's result has left dev_out[i]
+                grid.step(dev_in[i], dev_out[i], 0.0, stream=stream)
+                ev_step[i].record(stream)
+                s_down.wait_event(ev_step[i])
+                with torch.cuda.stream(s_down):
+                    for dst, src in zip(hout[i], dev_out[i]):
+                        dst.copy_(src, non_blocking=True)
+                ev_down[i].record(s_down)
+            stream.wait_stream(s_up)
+            stream.wait_stream(s_down)
             e1.record(stream)
             barrier()
             ems = max_over_ranks_(e0.elapsed_time(e1))
