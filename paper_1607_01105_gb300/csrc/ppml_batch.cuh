@@ -23,20 +23,6 @@ struct InstDev {
   int done, pad;
 };
 
-// Parabolas of the cells left and right of a face from the six values q[0..5] around it
-// (face between q[2] and q[3]): Appendix Steps 1-3.
-template <typename T>
-__device__ __forceinline__ void pair_parabolas(const T q[6], Parab<T>& PL, Parab<T>& PR) {
-  T d[4];
-#pragma unroll
-  for (int k = 1; k <= 4; k++) d[k - 1] = limited_slope(q[k - 1], q[k], q[k + 1]);
-  const T f12 = face_value(q[1], q[2], d[0], d[1]);
-  const T f23 = face_value(q[2], q[3], d[1], d[2]);
-  const T f34 = face_value(q[3], q[4], d[2], d[3]);
-  PL = parabola(q[2], f12, f23);
-  PR = parabola(q[3], f23, f34);
-}
-
 template <typename T>
 __device__ __forceinline__ void fill_ghosts_1d(T* q, int n) {
   const int t = threadIdx.x;
@@ -51,6 +37,69 @@ template <typename T>
 __device__ __forceinline__ T template_1d(T v) {
   const T four = v + v + v + v;
   return four / T(16) + four / T(8) + v / T(4);
+}
+
+// Parabolas of two quantities along a contiguous run of faces, streamed (Appendix Steps 1-3):
+// for faces f = f0 .. f1 (face f between cells f-1 and f) calls
+// on_face(f, a[f-1], a[f], Pa[f-1], Pa[f], b[f-1], b[f], Pb[f-1], Pb[f]).  qa(k), qb(k) give
+// cell k's values for k = f0-3 .. f1+2.  Each slope, face value and parabola is formed once,
+// with the same operations as per face.
+template <typename T, typename QA, typename QB, typename OF>
+__device__ __forceinline__ void stream_faces2(QA qa, QB qb, int f0, int f1, OF on_face) {
+  T a0 = qa(f0 - 3), a1 = qa(f0 - 2), a2 = qa(f0 - 1), a3 = qa(f0), a4 = qa(f0 + 1);
+  T b0 = qb(f0 - 3), b1 = qb(f0 - 2), b2 = qb(f0 - 1), b3 = qb(f0), b4 = qb(f0 + 1);
+  const T da1 = limited_slope(a0, a1, a2), db1 = limited_slope(b0, b1, b2);  // cell f0-2
+  T da2 = limited_slope(a1, a2, a3), db2 = limited_slope(b1, b2, b3);        // cell f0-1
+  T da3 = limited_slope(a2, a3, a4), db3 = limited_slope(b2, b3, b4);        // cell f0
+  const T fa1 = face_value(a1, a2, da1, da2), fb1 = face_value(b1, b2, db1, db2);  // face f0-1
+  T fa2 = face_value(a2, a3, da2, da3), fb2 = face_value(b2, b3, db2, db3);        // face f0
+  Parab<T> Pa = parabola(a2, fa1, fa2), Pb = parabola(b2, fb1, fb2);             // cell f0-1
+  (void)da2;
+  (void)db2;
+  for (int f = f0; f <= f1; f++) {
+    // window: a2 = cell f-1, a3 = cell f, a4 = cell f+1; da3 slope of f; fa2 face f
+    const T an = qa(f + 2), bn = qb(f + 2);
+    const T dan = limited_slope(a3, a4, an), dbn = limited_slope(b3, b4, bn);  // cell f+1
+    const T fan = face_value(a3, a4, da3, dan), fbn = face_value(b3, b4, db3, dbn);  // face f+1
+    const Parab<T> Qa = parabola(a3, fa2, fan), Qb = parabola(b3, fb2, fbn);       // cell f
+    on_face(f, a2, a3, Pa, Qa, b2, b3, Pb, Qb);
+    a2 = a3;
+    a3 = a4;
+    a4 = an;
+    b2 = b3;
+    b3 = b4;
+    b4 = bn;
+    da3 = dan;
+    db3 = dbn;
+    fa2 = fan;
+    fb2 = fbn;
+    Pa = Qa;
+    Pb = Qb;
+  }
+}
+
+// One quantity, as stream_faces2: on_face(f, Pq[f-1], Pq[f]).
+template <typename T, typename QF, typename OF>
+__device__ __forceinline__ void stream_faces(QF q, int f0, int f1, OF on_face) {
+  T a0 = q(f0 - 3), a1 = q(f0 - 2), a2 = q(f0 - 1), a3 = q(f0), a4 = q(f0 + 1);
+  const T d1 = limited_slope(a0, a1, a2);  // cell f0-2
+  const T d2 = limited_slope(a1, a2, a3);  // cell f0-1
+  T d3 = limited_slope(a2, a3, a4);        // cell f0
+  const T f1v = face_value(a1, a2, d1, d2);  // face f0-1
+  T f2v = face_value(a2, a3, d2, d3);        // face f0
+  Parab<T> P = parabola(a2, f1v, f2v);       // cell f0-1
+  for (int f = f0; f <= f1; f++) {
+    const T an = q(f + 2);
+    const T dn = limited_slope(a3, a4, an);
+    const T fn = face_value(a3, a4, d3, dn);
+    const Parab<T> Q = parabola(a3, f2v, fn);
+    on_face(f, P, Q);
+    a3 = a4;
+    a4 = an;
+    d3 = dn;
+    f2v = fn;
+    P = Q;
+  }
 }
 
 // v = m / rho: approximate reciprocal in FP32 (as in the stage kernels), IEEE in FP64.
@@ -142,6 +191,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
   }
   __syncthreads();
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
+  // faces per streamed run: one run per thread covers all n + 1 faces; at least 8 (the
+  // stream reads 3 extra cells on each side of its run)
+  const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS);
   for (int s = 0; s < max_steps; s++) {
     // CFL step of the current state (Sec. 1.1), per cell in the checker's order
     double vm = 0.0, cm = 0.0;
@@ -174,37 +226,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
     fill_ghosts_1d(E, n);
     fill_ghosts_1d(Ei, n);
     __syncthreads();
-    // Eulerian stage: faces f = 0..n between padded cells f+2 and f+3
-    for (int f = tid; f <= n; f += blockDim.x) {
-      T v[6], p[6];
-#pragma unroll
-      for (int q = 0; q < 6; q++) {
-        v[q] = vel_of(M[f + q], R[f + q]);
-        p[q] = gm1 * Ei[f + q];
+    // Eulerian stage: faces f = 0..n (between cells f-1 and f, padded cells f+2 and f+3);
+    // each thread streams one run of `run` consecutive faces
+    {
+      auto vq = [&](int k) { return vel_of(M[k + kBatchGhost], R[k + kBatchGhost]); };
+      auto pq = [&](int k) { return gm1 * Ei[k + kBatchGhost]; };
+      for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
+        const int f1 = min(f0 + run - 1, n);
+        stream_faces2<T>(vq, pq, f0, f1,
+                         [&](int f, T, T, const Parab<T>& vL, const Parab<T>& vR, T pl, T pr,
+                             const Parab<T>& pL, const Parab<T>& pR) {
+          const T rl = R[f + 2], rr = R[f + 3];
+          T V, P;
+          if constexpr (sizeof(T) == 4) {
+            float lam, Z, hrz;
+            face_constants_f32(rl, rr, sqrt_approx(rl), sqrt_approx(rr), pl, pr, gamma, lam, Z,
+                               hrz);
+            const float y = lam * th;
+            const float vls = avg_right(vL.R, vL.D, vL.S, y), vrs = avg_left(vR.L, vR.D, vR.S, y);
+            const float pls = avg_right(pL.R, pL.D, pL.S, y), prs = avg_left(pR.L, pR.D, pR.S, y);
+            V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
+            P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
+          } else {
+            T lam, Z;
+            face_constants(rl, rr, pl, pr, gamma, lam, Z);
+            const T y = Prec<T>::courant(lam, dt, I.h, th);
+            riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
+                       avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
+          }
+          FA[f] = V;
+          FB[f] = P;
+        });
       }
-      Parab<T> vL, vR, pL, pR;
-      pair_parabolas(v, vL, vR);
-      pair_parabolas(p, pL, pR);
-      T V, P;
-      if constexpr (sizeof(T) == 4) {
-        const float rl = R[f + 2], rr = R[f + 3];
-        float lam, Z, hrz;
-        face_constants_f32(rl, rr, sqrt_approx(rl), sqrt_approx(rr), p[2], p[3], gamma, lam, Z,
-                           hrz);
-        const float y = lam * th;
-        const float vls = avg_right(vL.R, vL.D, vL.S, y), vrs = avg_left(vR.L, vR.D, vR.S, y);
-        const float pls = avg_right(pL.R, pL.D, pL.S, y), prs = avg_left(pR.L, pR.D, pR.S, y);
-        V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
-        P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
-      } else {
-        T lam, Z;
-        face_constants(R[f + 2], R[f + 3], p[2], p[3], gamma, lam, Z);
-        const T y = Prec<T>::courant(lam, dt, I.h, th);
-        riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
-                   avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
-      }
-      FA[f] = V;
-      FB[f] = P;
     }
     __syncthreads();
     for (int c = tid; c < n; c += blockDim.x) {
@@ -237,15 +290,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
 #pragma unroll 1
     for (int k = 0; k < 4; k++) {
       T* q = fields[k];
-      for (int f = tid; f <= n; f += blockDim.x) {
-        T w[6];
-#pragma unroll
-        for (int o = 0; o < 6; o++) w[o] = q[f + o];
-        Parab<T> PL, PR;
-        pair_parabolas(w, PL, PR);
-        const T vh = FA[f];
-        const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
-        FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y) : vh * avg_left(PR.L, PR.D, PR.S, y);
+      auto qq = [&](int c) { return q[c + kBatchGhost]; };
+      for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
+        const int f1 = min(f0 + run - 1, n);
+        stream_faces<T>(qq, f0, f1, [&](int f, const Parab<T>& PL, const Parab<T>& PR) {
+          const T vh = FA[f];
+          const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
+          FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y)
+                             : vh * avg_left(PR.L, PR.D, PR.S, y);
+        });
       }
       __syncthreads();
       for (int c = tid; c < n; c += blockDim.x)
