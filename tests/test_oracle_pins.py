@@ -726,3 +726,45 @@ def test_isolated_poisson_fourth_order_as_table1():
         assert 15.0 <= pa / pb <= 17.0  # the golden values themselves are fourth order
     p = [_table1_case(n, printed_rhs=True) for n in (16, 32)]
     assert 3.5 <= p[0] / p[1] <= 4.5, p
+
+
+# ------------------------------------------------------- disk Fourier amplitudes (NEXT)
+
+def test_fourier_amplitudes_axisymmetric_disk_is_zero():
+    """An axisymmetric disk has all A_m = 0 (the paper's statement).  On a square grid
+    centred on the axis the sum over the four quarter-turn images of a column cancels
+    e^{i m phi} exactly unless m is a multiple of 4, so those amplitudes vanish to
+    round-off; A_4 and A_8 only carry the grid's own anisotropy."""
+    from oracle import disk
+    n, h = 96, 1.0 / 96
+    c = (np.arange(n) + 0.5 - 0.5 * n) * h
+    z, y, x = np.meshgrid(c[:8], c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y)
+    rho = np.exp(-r / 0.125) * np.exp(-(z / 0.02) ** 2) + 1e-6
+    a = disk.fourier_amplitudes(rho, h, 0.25, 8)
+    for m in range(1, 9):
+        if m % 4:
+            assert a[m - 1] < 1e-13, (m, a[m - 1])
+        else:
+            assert a[m - 1] < 1e-2, (m, a[m - 1])
+
+
+@pytest.mark.parametrize("m0", [2, 3, 7])
+def test_fourier_amplitudes_single_mode(m0):
+    """Sigma = f(r) (1 + eps cos(m0 phi - phi0)) gives A_m0 = eps / 2 in the continuum
+    (within the grid's quadrature error).  The quarter-turn images of a column cancel every
+    mode m whose parity differs from m0's (and that is not a multiple of 4, which the
+    axisymmetric part feeds through the grid's anisotropy) to round-off."""
+    from oracle import disk
+    n, h = 256, 1.0 / 256
+    c = (np.arange(n) + 0.5 - 0.5 * n) * h
+    y, x = np.meshgrid(c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y)
+    eps, phi0 = 0.1, 0.3
+    sigma = np.exp(-r / 0.125) * (1.0 + eps * np.cos(m0 * np.arctan2(y, x) - phi0))
+    rho = np.stack([sigma / h, sigma * 0.0 + 1e-12])  # two cells per column
+    a = disk.fourier_amplitudes(rho, h, 0.25, 8)
+    assert abs(a[m0 - 1] - eps / 2) <= 0.01 * eps / 2, a
+    for m in range(1, 9):
+        if (m - m0) % 2 and m % 4:
+            assert a[m - 1] < 1e-13, (m, a)
