@@ -142,6 +142,19 @@ int ppml_step_phi(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const
  * Asynchronous. */
 int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, double G, void* stream);
 
+/* Global Fourier amplitudes of a disk (paper, section on the gravitationally unstable
+ * disks, eq. of A_m(t)): A_m = |sum Sigma e^{i m phi}| / sum Sigma over the columns whose
+ * centre is within r_f of the z axis, Sigma the column density (sum over z of rho h_z) and
+ * phi = atan2(y, x) of the column centre, for m = 1..m_max (1 <= m_max <=
+ * PPML_FOURIER_MAX_MODES).  Column (i, j) is centred at ((i + 1/2 - nx/2) h_x,
+ * (j + 1/2 - ny/2) h_y): the grid is centred on the axis.  rho: device array of the grid's
+ * type.  Sums in FP64 in a fixed order.  Writes a_out[m_max] on the host; synchronizes the
+ * stream.  PPML_E_INVAL for bad arguments or no mass within r_f.  Buffers of about 0.3 MB
+ * are created on the first call and kept in the handle. */
+#define PPML_FOURIER_MAX_MODES 16
+int ppml_fourier_amplitudes(ppml_grid* g, const void* rho, double r_f, int m_max, double* a_out,
+                            void* stream);
+
 /* Right-hand side exactly as printed (4 pi G h^2 rho; second-order accurate). */
 #define PPML_POISSON_PRINTED_RHS 1u
 

@@ -126,6 +126,8 @@ struct ppml_grid {
   double* tables;
   // isolated Poisson solve (ppml_poisson.cu)
   PoissonIso* iso;
+  // disk Fourier amplitudes (ppml_fourier.cu)
+  FourierState* fourier;
 };
 
 int ppml_validate_desc(const ppml_grid_desc* d) {
@@ -346,6 +348,7 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
   if (g->spec) cudaFree(g->spec);
   if (g->tables) cudaFree(g->tables);
   ppml_iso_free(g->iso);
+  ppml_fourier_free(g->fourier);
   delete g;
   return PPML_OK;
 }
@@ -413,6 +416,16 @@ extern "C" int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, d
     if (fabs(g->d.h[a] - g->d.h[0]) > 1e-12 * g->d.h[0])
       return ppml_fail(PPML_E_INVAL, "the 27-point solve needs equal cell sizes");
   return ppml_iso_solve(&g->iso, &g->d, rho, phi, G, flags, (cudaStream_t)stream);
+}
+
+extern "C" int ppml_fourier_amplitudes(ppml_grid* g, const void* rho, double r_f, int m_max,
+                                       double* a_out, void* stream) {
+  ppml_clear_error();
+  if (!g || !rho || !a_out) return ppml_fail(PPML_E_INVAL, "grid, rho or a_out is NULL");
+  if (!(r_f > 0.0) || !isfinite(r_f)) return ppml_fail(PPML_E_INVAL, "r_f = %g must be > 0", r_f);
+  if (m_max < 1 || m_max > PPML_FOURIER_MAX_MODES)
+    return ppml_fail(PPML_E_INVAL, "m_max = %d not in [1, %d]", m_max, PPML_FOURIER_MAX_MODES);
+  return ppml_fourier_run(&g->fourier, &g->d, rho, r_f, m_max, a_out, (cudaStream_t)stream);
 }
 
 extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, void* stream) {

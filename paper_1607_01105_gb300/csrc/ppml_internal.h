@@ -20,3 +20,9 @@ struct PoissonIso;
 int ppml_iso_solve(PoissonIso** state, const ppml_grid_desc* d, const void* rho, void* phi,
                    double G, unsigned flags, cudaStream_t st);
 void ppml_iso_free(PoissonIso* s);
+
+// Disk Fourier amplitudes (ppml_fourier.cu); buffers created on the first call.
+struct FourierState;
+int ppml_fourier_run(FourierState** state, const ppml_grid_desc* d, const void* rho, double r_f,
+                     int m_max, double* a_out, cudaStream_t st);
+void ppml_fourier_free(FourierState* s);

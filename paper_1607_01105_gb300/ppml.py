@@ -29,7 +29,7 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
-            "ppml_batch_set_threads")
+            "ppml_batch_set_threads", "ppml_fourier_amplitudes")
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -76,6 +76,8 @@ _lib.ppml_poisson_isolated.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_
 _lib.ppml_batch_tune.argtypes = [_vp, ctypes.c_void_p * 4, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_batch_set_threads.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_fourier_amplitudes.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -194,6 +196,16 @@ class Grid:
                 raise ValueError("rho and phi must be contiguous CUDA tensors of the grid's dtype and size")
         _check(_lib.ppml_poisson_isolated(self._h, rho.data_ptr(), phi.data_ptr(), float(G),
                                           POISSON_PRINTED_RHS if printed_rhs else 0, _stream(stream)))
+
+    def fourier_amplitudes(self, rho, r_f, m_max=8, stream=None):
+        """Global Fourier amplitudes A_1..A_m_max of the column density within r_f of the
+        z axis (the grid is centred on the axis).  Synchronizes."""
+        if not rho.is_cuda or rho.dtype != self.tdtype or rho.numel() != self.cells or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous CUDA tensor of the grid's dtype and size")
+        out = (ctypes.c_double * int(m_max))()
+        _check(_lib.ppml_fourier_amplitudes(self._h, rho.data_ptr(), float(r_f), int(m_max), out,
+                                            _stream(stream)))
+        return list(out)
 
     def eulerian_stage(self, u_in, u_star, dt, stream=None):
         a = _state(u_in, self.tdtype, self.cells)

@@ -703,6 +703,28 @@ def test_config5_disk_64_fp64():
     compare(got, ref, TOL64)
 
 
+@pytest.mark.parametrize("n,dtype", [(64, F64), (64, F32), pytest.param(512, F32, marks=pytest.mark.slow)])
+def test_disk_fourier_amplitudes_match_oracle(n, dtype):
+    """Global Fourier amplitudes A_1..A_8 of the galactic disk (with its seeded 1 %
+    perturbation) within R_f = 0.25 against the oracle, on the same stored values
+    (relative 1e-10; the sums differ only in order and in how cos / sin of m phi are
+    formed); invalid arguments are rejected."""
+    from oracle import disk
+    pb = inputs.galactic_disk(n=n)
+    rho = np.asarray(pb.u[0], dtype=np.float64)
+    if dtype == F32:
+        rho = rho.astype(np.float32).astype(np.float64)
+    ref = disk.fourier_amplitudes(rho.reshape(n, n, n), pb.h[0], 0.25, 8)
+    u = ppml.to_device(pb.u, dtype)
+    grid = gpu_grid(pb, dtype, u)
+    got = np.array(grid.fourier_amplitudes(u[0], 0.25, 8))
+    assert np.all(np.abs(got - ref) <= 1e-10 * np.maximum(ref, 1e-6)), (got, ref)
+    assert got.max() < 0.1  # a 1 % perturbation of a near-axisymmetric disk
+    for bad in ((0.25, 0), (0.25, 17), (0.0, 4)):
+        with pytest.raises(ppml.PPMLError):
+            grid.fourier_amplitudes(u[0], *bad)
+
+
 def test_config5_disk_64_fp64_isolated_gravity():
     """The disk with self-gravity from the isolated-boundary solve (the paper's isolated
     galaxy setup) at 64^3 in FP64, 12 steps against the oracle (1e-10)."""
