@@ -113,41 +113,6 @@ __device__ __forceinline__ Parab<T> flat_parabola(T q) {
   return p;
 }
 
-// Lagrangian sweep of one field along one line.  q(p) returns the field at position p in
-// [-3, 18]; vh(c) is the face velocity between cells c-1 and c (c = 0..16).  emit(c, d) is
-// called for c = 0..15 with d = th * (F(c+1/2) - F(c-1/2)).
-template <typename T, typename QF, typename VF, typename EF>
-__device__ __forceinline__ void sweep_lagrangian(QF q, VF vh, T th, double tau, double h,
-                                                 EF emit) {
-  T qa = q(-3), qb = q(-2);  // q(p-2), q(p-1)
-  T da = T(0), fa = T(0);    // slope(p-2), face(p-5/2)
-  T PR = T(0), PD = T(0), PS = T(0), Fp = T(0);
-#pragma unroll
-  for (int p = -1; p <= TB + 2; p++) {
-    const T qn = q(p);
-    const T dn = limited_slope(qa, qb, qn);  // slope(p-1)
-    T fn = T(0);
-    if (p >= 0) fn = face_value(qa, qb, da, dn);  // face(p-3/2)
-    if (p >= 1) {
-      const Parab<T> P = parabola(qa, fa, fn);  // cell p-2
-      if (p >= 2) {
-        const T v = vh(p - 2);  // face between cells p-3 and p-2
-        const T y = Prec<T>::courant(tabs(v), tau, h, th);
-        const T F = v >= T(0) ? v * avg_right(PR, PD, PS, y) : v * avg_left(P.L, P.D, P.S, y);
-        if (p >= 3) emit(p - 3, th * (F - Fp));
-        Fp = F;
-      }
-      PR = P.R;
-      PD = P.D;
-      PS = P.S;
-    }
-    qa = qb;
-    qb = qn;
-    da = dn;
-    fa = fn;
-  }
-}
-
 // Eulerian sweep along one line: v(p), pr(p), r(p) give v_a, p and rho at position p.
 // emit(c, dm, dpv, dv) is called for cells c = 0..15 with dm = th (P+ - P-),
 // dpv = th (P+V+ - P-V-), dv = th (V+ - V-).
