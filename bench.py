@@ -239,6 +239,22 @@ def main():
                         "threads": b_threads, "tune_ms": {str(k): v for k, v in b_tune.items()}}
     batch.close()
     del bst
+    # the same batch in FP64 (its own autotuned CTA size)
+    bst64 = [torch.as_tensor(x).to(dev, torch.float64) for x in bb.u]
+    batch64 = ppml.Batch(bb.ncells, bb.h, bb.t_end, bb.gamma, bb.cfl, ppml.PPML_F64)
+    b64_threads, _ = batch64.tune(bst64, trial_steps=5, stream=stream)
+    barrier()
+    b0.record(stream)
+    batch64.step(bst64, 1 << 30)
+    b1.record(stream)
+    barrier()
+    b64ms = b0.elapsed_time(b1)
+    _, b64_steps = batch64.status()
+    results["batch64"] = {"ms": max_over_ranks_(b64ms), "threads": b64_threads,
+                          "updates": float(np.dot(bb.ncells.astype(np.float64),
+                                                  np.asarray(b64_steps, dtype=np.float64)))}
+    batch64.close()
+    del bst64
     for dtype, name in ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64")):
         elt = 4 if dtype == ppml.PPML_F32 else 8
         u = ppml.to_device(pb.u, dtype)
@@ -391,6 +407,10 @@ def main():
                               "cells": results["batch"]["cells"],
                               "finished": results["batch"]["done"], "dtype": "f32",
                               "cta_threads": results["batch"]["threads"],
+                              "fp64": {"value": results["batch64"]["updates"]
+                                       / (results["batch64"]["ms"] * 1e-3) / 1e6,
+                                       "ms": results["batch64"]["ms"],
+                                       "cta_threads": results["batch64"]["threads"]},
                               "tune_ms_20_steps": results["batch"]["tune_ms"],
                               "workload": "512 uneven 1D Riemann problems (128..4096 cells), "
                                           "each run to its own end time in one persistent launch"},
