@@ -111,7 +111,11 @@ __device__ __forceinline__ T vel_of(T m, T r) {
     return m / r;
 }
 
-__device__ __forceinline__ double block_max_sum(double a, double b, double* sh) {
+// CFL step of the CTA's instance (Sec. 1.1): the CTA maxima a = max|v|, b = max c, then
+// thread 0 forms dt = cfl h / (a + b), clipped to rem, and dt / h (the only FP64 divisions
+// of the step) and shares them.
+__device__ __forceinline__ void block_cfl_step(double a, double b, double cfl, double h,
+                                               double rem, double* sh, double& dt, double& th) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
@@ -129,13 +133,18 @@ __device__ __forceinline__ double block_max_sum(double a, double b, double* sh) 
       A = fmax(A, sh[q]);
       B = fmax(B, sh[32 + q]);
     }
-    sh[64] = A + B;
+    const double den = A + B;
+    double d = cfl * h / den;
+    if (d > rem) d = rem;
+    sh[64] = d;
+    sh[65] = d / h;
   }
   __syncthreads();
-  const double r = sh[64];
+  dt = sh[64];
+  th = sh[65];
   __syncthreads();
-  return r;
 }
+
 
 // Vacuum threshold of every instance (Sec. 1.4: a fraction of the mean density; the
 // fraction is stored negated until this kernel has run): the instance's mean initial
@@ -191,12 +200,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
   }
   __syncthreads();
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
-  // faces per streamed run: one run per thread covers all n + 1 faces; at least 8 (the
-  // stream reads 3 extra cells on each side of its run)
-  const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS);
+  // faces per streamed run: one run per thread covers all n + 1 faces; at least 9 (the
+  // stream reads 3 extra cells on each side of its run) and odd, so that the runs of the
+  // 32 lanes of a warp start on 32 different banks
+  const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS) | 1;
+  const float rho_vac_up = __double2float_ru(I.rho_vac);  // set by batch_vacuum_kernel
   for (int s = 0; s < max_steps; s++) {
     // CFL step of the current state (Sec. 1.1), per cell in the checker's order
-    double vm = 0.0, cm = 0.0;
+    T vm = T(0), cm = T(0);
     for (int c = tid; c < n; c += blockDim.x) {
       const T r = R[c + kBatchGhost];
       const T p = gm1 * Ei[c + kBatchGhost];
@@ -210,17 +221,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         v = sqrt(vx * vx + vy * vy + vz * vz);
         cs = sqrt(gamma * p / r);
       }
-      vm = fmax(vm, (double)v);
-      cm = fmax(cm, (double)cs);
+      vm = fmax(vm, v);
+      cm = fmax(cm, cs);
     }
-    const double den = block_max_sum(vm, cm, red);
-    double dt = cfl * I.h / den;
-    if (dt > I.t_end - I.t) dt = I.t_end - I.t;
+    double dt, thd;  // the maxima convert to double exactly
+    block_cfl_step((double)vm, (double)cm, cfl, I.h, I.t_end - I.t, red, dt, thd);
     if (!(dt > 0.0)) {
       I.done = 1;
       break;
     }
-    const T th = T(dt / I.h);
+    const T th = T(thd);
     fill_ghosts_1d(R, n);
     fill_ghosts_1d(M, n);
     fill_ghosts_1d(E, n);
@@ -309,7 +319,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
     for (int c = tid; c < n; c += blockDim.x) {
       const int g = c + kBatchGhost;
       T u[6] = {R[g], M[g], T(0), T(0), E[g], Ei[g]};
-      correct_energy<T>(u, I.rho_vac);
+      if constexpr (sizeof(T) == 4)
+        correct_energy_f32(u, rho_vac_up, I.rho_vac);
+      else
+        correct_energy<T>(u, I.rho_vac);
       M[g] = u[1];
       Ei[g] = u[5];
     }
