@@ -56,6 +56,7 @@ __device__ __forceinline__ void stream_faces2(QA qa, QB qb, int f0, int f1, OF o
   Parab<T> Pa = parabola(a2, fa1, fa2), Pb = parabola(b2, fb1, fb2);             // cell f0-1
   (void)da2;
   (void)db2;
+#pragma unroll 2
   for (int f = f0; f <= f1; f++) {
     // window: a2 = cell f-1, a3 = cell f, a4 = cell f+1; da3 slope of f; fa2 face f
     const T an = qa(f + 2), bn = qb(f + 2);
@@ -88,6 +89,7 @@ __device__ __forceinline__ void stream_faces(QF q, int f0, int f1, OF on_face) {
   const T f1v = face_value(a1, a2, d1, d2);  // face f0-1
   T f2v = face_value(a2, a3, d2, d3);        // face f0
   Parab<T> P = parabola(a2, f1v, f2v);       // cell f0-1
+#pragma unroll 2
   for (int f = f0; f <= f1; f++) {
     const T an = q(f + 2);
     const T dn = limited_slope(a3, a4, an);
