@@ -238,7 +238,10 @@ typedef struct ppml_batch ppml_batch;
 
 /* ncells[n_inst] (each >= 4), h[n_inst] (> 0), t_end[n_inst] (> 0) are host arrays;
  * they are copied.  vacuum_frac <= 0 selects 1e-5 (reference: each instance's own mean
- * initial density, computed at the first ppml_batch_step). */
+ * initial density, computed at the first ppml_batch_step).  The largest instance (n cells)
+ * must fit in one CTA's shared memory: 4 (n + 6) + 4 (n + 1) floats in FP32, 4 (n + 6) +
+ * 2 (n + 1) doubles in FP64, plus 1 KB, within the device's opt-in limit (on GB300 up to
+ * 7228 FP32 or 4817 FP64 cells); else PPML_E_INVAL. */
 int ppml_batch_init(int n_inst, const int* ncells, const double* h, const double* t_end,
                     double gamma, double cfl, double vacuum_frac, int dtype, ppml_batch** out);
 

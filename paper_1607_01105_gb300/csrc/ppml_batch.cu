@@ -81,7 +81,8 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
     off += ncells[i];
     nmax = std::max(nmax, ncells[i]);
   }
-  const size_t smem = (4 * (size_t)(nmax + 2 * kBatchGhost) + 2 * (size_t)(nmax + 1)) * elt;
+  const int nface = dtype == PPML_F64 ? kBatchFaceArrays<double> : kBatchFaceArrays<float>;
+  const size_t smem = (4 * (size_t)(nmax + 2 * kBatchGhost) + nface * (size_t)(nmax + 1)) * elt;
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -14,6 +14,11 @@
 namespace ppml {
 
 constexpr int kBatchGhost = 3;
+// Face arrays of nmax + 1 values behind the four fields in shared memory.  FP32 holds the
+// four Lagrangian fluxes of a step at once (one flux pass and one update pass per step);
+// FP64 takes the fields in turn through two, so that 4096-cell instances fit in 227 KB.
+template <typename T>
+constexpr int kBatchFaceArrays = sizeof(T) == 4 ? 4 : 2;
 
 struct InstDev {
   long long off;  // first cell in the packed arrays
@@ -104,6 +109,50 @@ __device__ __forceinline__ void stream_faces(QF q, int f0, int f1, OF on_face) {
   }
 }
 
+// NQ quantities along a run of faces, as stream_faces2: on_face(f, l, r, PL, PR), where
+// l[j], r[j] are quantity j in cells f-1 and f and PL[j], PR[j] its parabolas there;
+// q(j, k) gives quantity j in cell k for k = f0-3 .. f1+2.
+template <typename T, int NQ, typename QN, typename OF>
+__device__ __forceinline__ void stream_faces_n(QN q, int f0, int f1, OF on_face) {
+  T a2[NQ], a3[NQ], a4[NQ], d3[NQ], fv[NQ];
+  Parab<T> P[NQ];
+#pragma unroll
+  for (int j = 0; j < NQ; j++) {
+    const T a0 = q(j, f0 - 3), a1 = q(j, f0 - 2);
+    a2[j] = q(j, f0 - 1);
+    a3[j] = q(j, f0);
+    a4[j] = q(j, f0 + 1);
+    const T d1 = limited_slope(a0, a1, a2[j]);      // cell f0-2
+    const T d2 = limited_slope(a1, a2[j], a3[j]);   // cell f0-1
+    d3[j] = limited_slope(a2[j], a3[j], a4[j]);     // cell f0
+    const T fl = face_value(a1, a2[j], d1, d2);     // face f0-1
+    fv[j] = face_value(a2[j], a3[j], d2, d3[j]);    // face f0
+    P[j] = parabola(a2[j], fl, fv[j]);              // cell f0-1
+  }
+#pragma unroll 2
+  for (int f = f0; f <= f1; f++) {
+    T an[NQ], dn[NQ], fn[NQ];
+    Parab<T> Q[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; j++) {
+      an[j] = q(j, f + 2);
+      dn[j] = limited_slope(a3[j], a4[j], an[j]);     // cell f+1
+      fn[j] = face_value(a3[j], a4[j], d3[j], dn[j]);  // face f+1
+      Q[j] = parabola(a3[j], fv[j], fn[j]);           // cell f
+    }
+    on_face(f, a2, a3, P, Q);
+#pragma unroll
+    for (int j = 0; j < NQ; j++) {
+      a2[j] = a3[j];
+      a3[j] = a4[j];
+      a4[j] = an[j];
+      d3[j] = dn[j];
+      fv[j] = fn[j];
+      P[j] = Q[j];
+    }
+  }
+}
+
 // v = m / rho: approximate reciprocal in FP32 (as in the stage kernels), IEEE in FP64.
 template <typename T>
 __device__ __forceinline__ T vel_of(T m, T r) {
@@ -113,38 +162,76 @@ __device__ __forceinline__ T vel_of(T m, T r) {
     return m / r;
 }
 
-// CFL step of the CTA's instance (Sec. 1.1): the CTA maxima a = max|v|, b = max c, then
-// thread 0 forms dt = cfl h / (a + b), clipped to rem, and dt / h (the only FP64 divisions
-// of the step) and shares them.
-__device__ __forceinline__ void block_cfl_step(double a, double b, double cfl, double h,
-                                               double rem, double* sh, double& dt, double& th) {
+// CFL step of the CTA's instance (Sec. 1.1) from the per-thread maxima a = max|v|,
+// b = max c: warp maxima, then warp 0 folds the warps' (maxima in the state's precision;
+// a maximum is exact in any).  Thread 0 alone keeps the instance's time (t, steps, done):
+// it stops the CTA once t has reached t_end, else forms tau clipped to the remaining time
+// and advances t.  FP64 forms tau = cfl h / (a + b) and tau / h as the checker does; FP32
+// forms tau / h = cfl / (a + b) in FP32 and tau = (tau / h) h in FP64 (both divisions of
+// the FP64 form, at the FP64 pipe's latency, would lie on every step's critical path).
+// Returns whether the CTA takes the step (the same in every thread), with th = tau / h
+// and, in FP64, dt = tau.  Two barriers; the caller puts at least one more between two
+// calls, so the next call's writes to sh cannot overtake this call's reads.
+template <typename T>
+__device__ __forceinline__ bool block_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
+                                               double& dt, T& th) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
     b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
   }
+  T* shT = reinterpret_cast<T*>(sh);  // 32 + 32 warp maxima
+  int* go_sh = reinterpret_cast<int*>(sh + 68);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    sh[w] = a;
-    sh[32 + w] = b;
+    shT[w] = a;
+    shT[32 + w] = b;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double A = 0.0, B = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
-      A = fmax(A, sh[q]);
-      B = fmax(B, sh[32 + q]);
+  if (w == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    T A = lane < nw ? shT[lane] : T(0), B = lane < nw ? shT[32 + lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      A = fmax(A, __shfl_down_sync(0xffffffffu, A, o));
+      B = fmax(B, __shfl_down_sync(0xffffffffu, B, o));
     }
-    const double den = A + B;
-    double d = cfl * h / den;
-    if (d > rem) d = rem;
-    sh[64] = d;
-    sh[65] = d / h;
+    if (lane == 0) {
+      int go = 0;
+      double d = 0.0;
+      T q = T(0);
+      if (!(I.t >= I.t_end)) {
+        const double rem = I.t_end - I.t;
+        if constexpr (sizeof(T) == 4) {
+          q = (float)cfl / (A + B);
+          d = (double)q * I.h;
+          if (d > rem) {
+            d = rem;
+            q = (float)(rem / I.h);
+          }
+        } else {
+          const double den = A + B;
+          d = cfl * I.h / den;
+          if (d > rem) d = rem;
+          q = d / I.h;
+        }
+        go = d > 0.0;
+      }
+      if (go) {
+        I.t = (I.t + d > I.t_end) ? I.t_end : I.t + d;
+        I.steps += 1;
+      } else {
+        I.done = 1;
+      }
+      sh[64] = d;
+      *reinterpret_cast<T*>(sh + 66) = q;
+      *go_sh = go;
+    }
   }
   __syncthreads();
   dt = sh[64];
-  th = sh[65];
-  __syncthreads();
+  th = *reinterpret_cast<const T*>(sh + 66);
+  return *go_sh != 0;
 }
 
 
@@ -191,53 +278,80 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
   T* M = R + stride;
   T* E = M + stride;
   T* Ei = E + stride;
-  T* FA = Ei + stride;      // face array A (V, then v hat)
+  T* FA = Ei + stride;      // face array A (V, then v hat or the rho flux)
   T* FB = FA + (nmax + 1);  // face array B (P, then fluxes)
+  T* FC = FB + (nmax + 1);  // FP32 only: the rho E and rho eps fluxes
+  T* FD = FC + (nmax + 1);
   const int tid = threadIdx.x;
-  for (int c = tid; c < n; c += blockDim.x) {
-    R[c + kBatchGhost] = g_rho[I.off + c];
-    M[c + kBatchGhost] = g_m[I.off + c];
-    E[c + kBatchGhost] = g_en[I.off + c];
-    Ei[c + kBatchGhost] = g_ei[I.off + c];
-  }
-  __syncthreads();
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
   // faces per streamed run: one run per thread covers all n + 1 faces; at least 9 (the
   // stream reads 3 extra cells on each side of its run) and odd, so that the runs of the
   // 32 lanes of a warp start on 32 different banks
   const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS) | 1;
   const float rho_vac_up = __double2float_ru(I.rho_vac);  // set by batch_vacuum_kernel
+  // The owner of an edge cell also writes that cell's outflow ghosts, in the same pass
+  // that writes the cell, so no pass of its own (and no barrier) refreshes them.
+  auto ghosts = [&](T* q, int c, T v) {
+    if (c == 0)
+#pragma unroll
+      for (int k = 0; k < kBatchGhost; k++) q[k] = v;
+    if (c == n - 1)
+#pragma unroll
+      for (int k = 0; k < kBatchGhost; k++) q[n + kBatchGhost + k] = v;
+  };
+  // CFL maxima (Sec. 1.1) over the cells a thread owns, taken as each cell's final value
+  // of a step is written: max |v| and max c, in the checker's per-cell operations
+  T vm = T(0), cm = T(0);
+  auto cfl_cell = [&](T r, T m, T ei) {
+    const T p = gm1 * ei;
+    T v, cs;
+    if constexpr (sizeof(T) == 4) {
+      const float ir = rcp_approx(r);
+      v = fabsf(m * ir);
+      cs = sqrt_approx(gamma * p * ir);
+    } else {
+      const T vx = m / r, vy = T(0) / r, vz = T(0) / r;
+      v = sqrt(vx * vx + vy * vy + vz * vz);
+      cs = sqrt(gamma * p / r);
+    }
+    vm = fmax(vm, v);
+    cm = fmax(cm, cs);
+  };
+  for (int c = tid; c < n; c += blockDim.x) {
+    const int g = c + kBatchGhost;
+    const T r = g_rho[I.off + c], m = g_m[I.off + c], en = g_en[I.off + c], ei = g_ei[I.off + c];
+    R[g] = r;
+    M[g] = m;
+    E[g] = en;
+    Ei[g] = ei;
+    ghosts(R, c, r);
+    ghosts(M, c, m);
+    ghosts(E, c, en);
+    ghosts(Ei, c, ei);
+    cfl_cell(r, m, ei);
+  }
+  // Upwind Lagrangian fluxes of one field at the faces of every thread's run (Sec. 1.3)
+  auto lagrangian_fluxes = [&](const T* q, double dt, T th) {
+    auto qq = [&](int c) { return q[c + kBatchGhost]; };
+    for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
+      const int f1 = min(f0 + run - 1, n);
+      stream_faces<T>(qq, f0, f1, [&](int f, const Parab<T>& PL, const Parab<T>& PR) {
+        const T vh = FA[f];
+        const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
+        FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y)
+                           : vh * avg_left(PR.L, PR.D, PR.S, y);
+      });
+    }
+  };
+  // Barriers per step: two in the CFL reduction (the first also orders every field and
+  // ghost write of the previous step), Eulerian faces, Eulerian update, then in FP32 one
+  // after the Lagrangian flux pass; in FP64 one after v hat and two per Lagrangian field
+  // but the last.  The last update pass also applies the energy correction, writes the
+  // ghosts and takes the next step's CFL maxima.
   for (int s = 0; s < max_steps; s++) {
-    // CFL step of the current state (Sec. 1.1), per cell in the checker's order
-    T vm = T(0), cm = T(0);
-    for (int c = tid; c < n; c += blockDim.x) {
-      const T r = R[c + kBatchGhost];
-      const T p = gm1 * Ei[c + kBatchGhost];
-      T v, cs;
-      if constexpr (sizeof(T) == 4) {
-        const float ir = rcp_approx(r);
-        v = fabsf(M[c + kBatchGhost] * ir);
-        cs = sqrt_approx(gamma * p * ir);
-      } else {
-        const T vx = M[c + kBatchGhost] / r, vy = T(0) / r, vz = T(0) / r;
-        v = sqrt(vx * vx + vy * vy + vz * vz);
-        cs = sqrt(gamma * p / r);
-      }
-      vm = fmax(vm, v);
-      cm = fmax(cm, cs);
-    }
-    double dt, thd;  // the maxima convert to double exactly
-    block_cfl_step((double)vm, (double)cm, cfl, I.h, I.t_end - I.t, red, dt, thd);
-    if (!(dt > 0.0)) {
-      I.done = 1;
-      break;
-    }
-    const T th = T(thd);
-    fill_ghosts_1d(R, n);
-    fill_ghosts_1d(M, n);
-    fill_ghosts_1d(E, n);
-    fill_ghosts_1d(Ei, n);
-    __syncthreads();
+    double dt;
+    T th;
+    if (!block_cfl_step<T>(vm, cm, cfl, I, red, dt, th)) break;
     // Eulerian stage: faces f = 0..n (between cells f-1 and f, padded cells f+2 and f+3);
     // each thread streams one run of `run` consecutive faces
     {
@@ -276,64 +390,107 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       const int g = c + kBatchGhost;
       const T Vm = FA[c], Vp = FA[c + 1], Pm = FB[c], Pp = FB[c + 1];
       const T ei0 = Ei[g];
-      M[g] = M[g] - th * (Pp - Pm);
-      E[g] = E[g] - th * (Pp * Vp - Pm * Vm);
-      Ei[g] = ei0 - gm1 * ei0 * (th * (Vp - Vm));
+      const T m1 = M[g] - th * (Pp - Pm);
+      const T e1 = E[g] - th * (Pp * Vp - Pm * Vm);
+      const T ei1 = ei0 - gm1 * ei0 * (th * (Vp - Vm));
+      M[g] = m1;
+      E[g] = e1;
+      Ei[g] = ei1;
+      ghosts(M, c, m1);
+      ghosts(E, c, e1);
+      ghosts(Ei, c, ei1);
     }
     __syncthreads();
-    fill_ghosts_1d(M, n);
-    fill_ghosts_1d(E, n);
-    fill_ghosts_1d(Ei, n);
-    __syncthreads();
-    // Lagrangian stage: v hat at faces, then each field's flux and update
-    for (int f = tid; f <= n; f += blockDim.x) {
-      const T rl = R[f + 2], rr = R[f + 3];
-      const T vtl = template_1d(vel_of(M[f + 2], rl)), vtr = template_1d(vel_of(M[f + 3], rr));
-      if constexpr (sizeof(T) == 4) {
-        const float sl = sqrt_approx(rl), sr = sqrt_approx(rr);
-        FA[f] = (vtr * sr + vtl * sl) * rcp_approx(sr + sl);
-      } else {
-        const T sl = sqrt(rl), sr = sqrt(rr);
-        FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
-      }
-    }
-    __syncthreads();
-    T* fields[4] = {R, M, E, Ei};
-#pragma unroll 1
-    for (int k = 0; k < 4; k++) {
-      T* q = fields[k];
-      auto qq = [&](int c) { return q[c + kBatchGhost]; };
+    if constexpr (sizeof(T) == 4) {
+      // Lagrangian stage in one pass over each run of faces: v hat (eq. veltemplate with
+      // the Roe weights, Sec. 1.3) from the streamed rho and m, each cell's template and
+      // sqrt(rho) formed once and carried to the next face, then the upwind fluxes of all
+      // four fields
+      auto q4 = [&](int j, int k) {
+        return (j == 0 ? R : j == 1 ? M : j == 2 ? E : Ei)[k + kBatchGhost];
+      };
       for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
         const int f1 = min(f0 + run - 1, n);
-        stream_faces<T>(qq, f0, f1, [&](int f, const Parab<T>& PL, const Parab<T>& PR) {
-          const T vh = FA[f];
-          const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
-          FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y)
-                             : vh * avg_left(PR.L, PR.D, PR.S, y);
+        const float r0 = R[f0 + 2];  // cell f0-1
+        float vt_l = template_1d(vel_of(M[f0 + 2], r0)), s_l = sqrt_approx(r0);
+        stream_faces_n<float, 4>(q4, f0, f1,
+                                 [&](int f, const float*, const float* c, const Parab<float>* PL,
+                                     const Parab<float>* PR) {
+          const float vt_r = template_1d(vel_of(c[1], c[0])), s_r = sqrt_approx(c[0]);
+          const float vh = (vt_r * s_r + vt_l * s_l) * rcp_approx(s_r + s_l);
+          vt_l = vt_r;
+          s_l = s_r;
+          const float y = Prec<float>::courant(tabs(vh), dt, I.h, th);
+          float F[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            F[j] = vh >= 0.0f ? vh * avg_right(PL[j].R, PL[j].D, PL[j].S, y)
+                              : vh * avg_left(PR[j].L, PR[j].D, PR[j].S, y);
+          FA[f] = F[0];
+          FB[f] = F[1];
+          FC[f] = F[2];
+          FD[f] = F[3];
         });
       }
       __syncthreads();
-      for (int c = tid; c < n; c += blockDim.x)
-        q[c + kBatchGhost] = q[c + kBatchGhost] - th * (FB[c + 1] - FB[c]);
-      __syncthreads();
-    }
-    // Sec. 1.4 energy consistency
-    for (int c = tid; c < n; c += blockDim.x) {
-      const int g = c + kBatchGhost;
-      T u[6] = {R[g], M[g], T(0), T(0), E[g], Ei[g]};
-      if constexpr (sizeof(T) == 4)
+      // every field's update, the Sec. 1.4 energy consistency, the ghosts and the next
+      // step's CFL maxima, cell by cell
+      vm = T(0);
+      cm = T(0);
+      for (int c = tid; c < n; c += blockDim.x) {
+        const int g = c + kBatchGhost;
+        const float r = R[g] - th * (FA[c + 1] - FA[c]);
+        const float en = E[g] - th * (FC[c + 1] - FC[c]);
+        float u[6] = {r, M[g] - th * (FB[c + 1] - FB[c]), 0.0f, 0.0f, en,
+                      Ei[g] - th * (FD[c + 1] - FD[c])};
         correct_energy_f32(u, rho_vac_up, I.rho_vac);
-      else
+        R[g] = r;
+        M[g] = u[1];
+        E[g] = en;
+        Ei[g] = u[5];
+        ghosts(R, c, r);
+        ghosts(M, c, u[1]);
+        ghosts(E, c, en);
+        ghosts(Ei, c, u[5]);
+        cfl_cell(r, u[1], u[5]);
+      }
+    } else {
+      // FP64 Lagrangian stage: v hat at faces, then each field's flux and update in turn
+      for (int f = tid; f <= n; f += blockDim.x) {
+        const T rl = R[f + 2], rr = R[f + 3];
+        const T vtl = template_1d(vel_of(M[f + 2], rl)), vtr = template_1d(vel_of(M[f + 3], rr));
+        const T sl = sqrt(rl), sr = sqrt(rr);
+        FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
+      }
+      __syncthreads();
+      T* fields[3] = {R, M, E};
+#pragma unroll 1
+      for (int k = 0; k < 3; k++) {
+        T* q = fields[k];
+        lagrangian_fluxes(q, dt, th);
+        __syncthreads();
+        for (int c = tid; c < n; c += blockDim.x)
+          q[c + kBatchGhost] = q[c + kBatchGhost] - th * (FB[c + 1] - FB[c]);
+        __syncthreads();
+      }
+      lagrangian_fluxes(Ei, dt, th);
+      __syncthreads();
+      // rho eps update, then the Sec. 1.4 energy consistency, on the same cells
+      vm = T(0);
+      cm = T(0);
+      for (int c = tid; c < n; c += blockDim.x) {
+        const int g = c + kBatchGhost;
+        const T r = R[g], en = E[g];
+        T u[6] = {r, M[g], T(0), T(0), en, Ei[g] - th * (FB[c + 1] - FB[c])};
         correct_energy<T>(u, I.rho_vac);
-      M[g] = u[1];
-      Ei[g] = u[5];
-    }
-    __syncthreads();
-    I.t = (I.t + dt > I.t_end) ? I.t_end : I.t + dt;
-    I.steps += 1;
-    if (I.t >= I.t_end) {
-      I.done = 1;
-      break;
+        M[g] = u[1];
+        Ei[g] = u[5];
+        ghosts(R, c, r);
+        ghosts(M, c, u[1]);
+        ghosts(E, c, en);
+        ghosts(Ei, c, u[5]);
+        cfl_cell(r, u[1], u[5]);
+      }
     }
   }
   for (int c = tid; c < n; c += blockDim.x) {
@@ -342,7 +499,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
     g_en[I.off + c] = E[c + kBatchGhost];
     g_ei[I.off + c] = Ei[c + kBatchGhost];
   }
-  if (tid == 0) inst[id] = I;
+  if (tid == 0) {  // thread 0's copy holds the instance's time
+    if (I.t >= I.t_end) I.done = 1;
+    inst[id] = I;
+  }
 }
 
 }  // namespace ppml
