@@ -111,7 +111,8 @@ __device__ __forceinline__ void stream_faces(QF q, int f0, int f1, OF on_face) {
 
 // NQ quantities along a run of faces, as stream_faces2: on_face(f, l, r, PL, PR), where
 // l[j], r[j] are quantity j in cells f-1 and f and PL[j], PR[j] its parabolas there;
-// q(j, k) gives quantity j in cell k for k = f0-3 .. f1+2.
+// q(j, k) gives quantity j in cell k for k = f0-3 .. f1+2, each read one face ahead of its
+// use (so that the read overlaps the previous face's stores).
 template <typename T, int NQ, typename QN, typename OF>
 __device__ __forceinline__ void stream_faces_n(QN q, int f0, int f1, OF on_face) {
   T a2[NQ], a3[NQ], a4[NQ], d3[NQ], fv[NQ];
@@ -129,13 +130,17 @@ __device__ __forceinline__ void stream_faces_n(QN q, int f0, int f1, OF on_face)
     fv[j] = face_value(a2[j], a3[j], d2, d3[j]);    // face f0
     P[j] = parabola(a2[j], fl, fv[j]);              // cell f0-1
   }
-#pragma unroll 2
+  T pa[NQ];  // cell f+2, read one face ahead
+#pragma unroll
+  for (int j = 0; j < NQ; j++) pa[j] = q(j, f0 + 2);
+#pragma unroll 4
   for (int f = f0; f <= f1; f++) {
     T an[NQ], dn[NQ], fn[NQ];
     Parab<T> Q[NQ];
 #pragma unroll
     for (int j = 0; j < NQ; j++) {
-      an[j] = q(j, f + 2);
+      an[j] = pa[j];
+      if (f < f1) pa[j] = q(j, f + 3);
       dn[j] = limited_slope(a3[j], a4[j], an[j]);     // cell f+1
       fn[j] = face_value(a3[j], a4[j], d3[j], dn[j]);  // face f+1
       Q[j] = parabola(a3[j], fv[j], fn[j]);           // cell f
@@ -288,21 +293,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
   // stream reads 3 extra cells on each side of its run) and odd, so that the runs of the
   // 32 lanes of a warp start on 32 different banks
   const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS) | 1;
+  constexpr int kU = sizeof(T) == 4 ? 4 : 2;  // cells per thread per update pass
   const float rho_vac_up = __double2float_ru(I.rho_vac);  // set by batch_vacuum_kernel
-  // The owner of an edge cell also writes that cell's outflow ghosts, in the same pass
-  // that writes the cell, so no pass of its own (and no barrier) refreshes them.
-  auto ghosts = [&](T* q, int c, T v) {
-    if (c == 0)
+  // Outflow ghosts of field q from its edge cells, written after a cell pass by the
+  // threads that own those cells (cell c belongs to thread c mod NTHREADS in every cell
+  // pass): they read back their own stores, so no barrier (and no pass) of its own.
+  const int owner_last = (n - 1) % NTHREADS;
+  auto edge_ghosts = [&](T* q) {
+    if (tid == 0) {
+      const T v = q[kBatchGhost];
 #pragma unroll
       for (int k = 0; k < kBatchGhost; k++) q[k] = v;
-    if (c == n - 1)
+    }
+    if (tid == owner_last) {
+      const T v = q[n + kBatchGhost - 1];
 #pragma unroll
       for (int k = 0; k < kBatchGhost; k++) q[n + kBatchGhost + k] = v;
+    }
   };
   // CFL maxima (Sec. 1.1) over the cells a thread owns, taken as each cell's final value
   // of a step is written: max |v| and max c, in the checker's per-cell operations
   T vm = T(0), cm = T(0);
-  auto cfl_cell = [&](T r, T m, T ei) {
+  auto cfl_cell = [&](T r, T m, T ei, bool valid) {
     const T p = gm1 * ei;
     T v, cs;
     if constexpr (sizeof(T) == 4) {
@@ -314,8 +326,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       v = sqrt(vx * vx + vy * vy + vz * vz);
       cs = sqrt(gamma * p / r);
     }
-    vm = fmax(vm, v);
-    cm = fmax(cm, cs);
+    vm = valid ? fmax(vm, v) : vm;
+    cm = valid ? fmax(cm, cs) : cm;
   };
   for (int c = tid; c < n; c += blockDim.x) {
     const int g = c + kBatchGhost;
@@ -324,12 +336,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
     M[g] = m;
     E[g] = en;
     Ei[g] = ei;
-    ghosts(R, c, r);
-    ghosts(M, c, m);
-    ghosts(E, c, en);
-    ghosts(Ei, c, ei);
-    cfl_cell(r, m, ei);
+    cfl_cell(r, m, ei, true);
   }
+  edge_ghosts(R);
+  edge_ghosts(M);
+  edge_ghosts(E);
+  edge_ghosts(Ei);
   // Upwind Lagrangian fluxes of one field at the faces of every thread's run (Sec. 1.3)
   auto lagrangian_fluxes = [&](const T* q, double dt, T th) {
     auto qq = [&](int c) { return q[c + kBatchGhost]; };
@@ -359,15 +371,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       auto pq = [&](int k) { return gm1 * Ei[k + kBatchGhost]; };
       for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
         const int f1 = min(f0 + run - 1, n);
+        // rho and sqrt(rho) of the face's left cell, carried from the previous face
+        T r_l = R[f0 + 2], s_l = T(0);
+        if constexpr (sizeof(T) == 4) s_l = sqrt_approx(r_l);
         stream_faces2<T>(vq, pq, f0, f1,
                          [&](int f, T, T, const Parab<T>& vL, const Parab<T>& vR, T pl, T pr,
                              const Parab<T>& pL, const Parab<T>& pR) {
-          const T rl = R[f + 2], rr = R[f + 3];
+          const T rl = r_l, rr = R[f + 3];
+          r_l = rr;
           T V, P;
           if constexpr (sizeof(T) == 4) {
             float lam, Z, hrz;
-            face_constants_f32(rl, rr, sqrt_approx(rl), sqrt_approx(rr), pl, pr, gamma, lam, Z,
-                               hrz);
+            const float sl = s_l, sr = sqrt_approx(rr);
+            s_l = sr;
+            face_constants_f32(rl, rr, sl, sr, pl, pr, gamma, lam, Z, hrz);
             const float y = lam * th;
             const float vls = avg_right(vL.R, vL.D, vL.S, y), vrs = avg_left(vR.L, vR.D, vR.S, y);
             const float pls = avg_right(pL.R, pL.D, pL.S, y), prs = avg_left(pR.L, pR.D, pR.S, y);
@@ -386,20 +403,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       }
     }
     __syncthreads();
-    for (int c = tid; c < n; c += blockDim.x) {
-      const int g = c + kBatchGhost;
-      const T Vm = FA[c], Vp = FA[c + 1], Pm = FB[c], Pp = FB[c + 1];
-      const T ei0 = Ei[g];
-      const T m1 = M[g] - th * (Pp - Pm);
-      const T e1 = E[g] - th * (Pp * Vp - Pm * Vm);
-      const T ei1 = ei0 - gm1 * ei0 * (th * (Vp - Vm));
-      M[g] = m1;
-      E[g] = e1;
-      Ei[g] = ei1;
-      ghosts(M, c, m1);
-      ghosts(E, c, e1);
-      ghosts(Ei, c, ei1);
+    // cells c0 + u NTHREADS, u < kU, per pass: every load of the pass ahead of its stores
+    // (the compiler cannot move a load past a store into the same shared array)
+    for (int c0 = tid; c0 < n; c0 += kU * NTHREADS) {
+      T Vm[kU], Vp[kU], Pm[kU], Pp[kU], m0[kU], e0[kU], ei0[kU];
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const int c = min(c0 + u * NTHREADS, n - 1), g = c + kBatchGhost;
+        Vm[u] = FA[c];
+        Vp[u] = FA[c + 1];
+        Pm[u] = FB[c];
+        Pp[u] = FB[c + 1];
+        m0[u] = M[g];
+        e0[u] = E[g];
+        ei0[u] = Ei[g];
+      }
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const int c = c0 + u * NTHREADS, g = c + kBatchGhost;
+        if (c < n) {
+          const T m1 = m0[u] - th * (Pp[u] - Pm[u]);
+          const T e1 = e0[u] - th * (Pp[u] * Vp[u] - Pm[u] * Vm[u]);
+          const T ei1 = ei0[u] - gm1 * ei0[u] * (th * (Vp[u] - Vm[u]));
+          M[g] = m1;
+          E[g] = e1;
+          Ei[g] = ei1;
+        }
+      }
     }
+    edge_ghosts(M);
+    edge_ghosts(E);
+    edge_ghosts(Ei);
     __syncthreads();
     if constexpr (sizeof(T) == 4) {
       // Lagrangian stage in one pass over each run of faces: v hat (eq. veltemplate with
@@ -437,23 +471,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       // step's CFL maxima, cell by cell
       vm = T(0);
       cm = T(0);
-      for (int c = tid; c < n; c += blockDim.x) {
-        const int g = c + kBatchGhost;
-        const float r = R[g] - th * (FA[c + 1] - FA[c]);
-        const float en = E[g] - th * (FC[c + 1] - FC[c]);
-        float u[6] = {r, M[g] - th * (FB[c + 1] - FB[c]), 0.0f, 0.0f, en,
-                      Ei[g] - th * (FD[c + 1] - FD[c])};
-        correct_energy_f32(u, rho_vac_up, I.rho_vac);
-        R[g] = r;
-        M[g] = u[1];
-        E[g] = en;
-        Ei[g] = u[5];
-        ghosts(R, c, r);
-        ghosts(M, c, u[1]);
-        ghosts(E, c, en);
-        ghosts(Ei, c, u[5]);
-        cfl_cell(r, u[1], u[5]);
+      for (int c0 = tid; c0 < n; c0 += kU * NTHREADS) {
+        float q[kU][4];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+          const int c = min(c0 + u * NTHREADS, n - 1), g = c + kBatchGhost;
+          q[u][0] = R[g] - th * (FA[c + 1] - FA[c]);
+          q[u][1] = M[g] - th * (FB[c + 1] - FB[c]);
+          q[u][2] = E[g] - th * (FC[c + 1] - FC[c]);
+          q[u][3] = Ei[g] - th * (FD[c + 1] - FD[c]);
+        }
+        // Sec. 1.4: the dense branch for all kU cells without control flow (so that
+        // their chains interleave), then the rare vacuum cells
+        float w[kU][6];
+        bool vac[kU], any_vac = false;
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+          w[u][0] = q[u][0];
+          w[u][1] = q[u][1];
+          w[u][2] = 0.0f;
+          w[u][3] = 0.0f;
+          w[u][4] = q[u][2];
+          w[u][5] = q[u][3];
+          vac[u] = vacuum_cell_f32(w[u], rho_vac_up);
+          any_vac |= vac[u];
+          q[u][3] = dense_eps_f32(w[u]);
+        }
+        if (any_vac) {
+#pragma unroll
+          for (int u = 0; u < kU; u++)
+            if (vac[u]) {
+              vacuum_correct_f32(w[u], I.rho_vac);
+              q[u][1] = w[u][1];
+              q[u][3] = w[u][5];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+          const int c = c0 + u * NTHREADS, g = c + kBatchGhost;
+          if (c < n) {
+            R[g] = q[u][0];
+            M[g] = q[u][1];
+            E[g] = q[u][2];
+            Ei[g] = q[u][3];
+          }
+        }
+        // next step's CFL maxima over the valid cells (a clamped duplicate may have read
+        // a cell its owner has already updated)
+#pragma unroll
+        for (int u = 0; u < kU; u++) cfl_cell(q[u][0], q[u][1], q[u][3], c0 + u * NTHREADS < n);
       }
+      edge_ghosts(R);
+      edge_ghosts(M);
+      edge_ghosts(E);
+      edge_ghosts(Ei);
     } else {
       // FP64 Lagrangian stage: v hat at faces, then each field's flux and update in turn
       for (int f = tid; f <= n; f += blockDim.x) {
@@ -485,12 +556,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         correct_energy<T>(u, I.rho_vac);
         M[g] = u[1];
         Ei[g] = u[5];
-        ghosts(R, c, r);
-        ghosts(M, c, u[1]);
-        ghosts(E, c, en);
-        ghosts(Ei, c, u[5]);
-        cfl_cell(r, u[1], u[5]);
+        cfl_cell(r, u[1], u[5], true);
       }
+      edge_ghosts(R);
+      edge_ghosts(M);
+      edge_ghosts(E);
+      edge_ghosts(Ei);
     }
   }
   for (int c = tid; c < n; c += blockDim.x) {

@@ -258,19 +258,30 @@ __device__ __forceinline__ int correct_energy<double>(double u[6], double rho_va
 }
 // rho_vac_up = rho_vac rounded up to float: for any float x, x < rho_vac_up exactly when
 // x < rho_vac (no float lies in [rho_vac, rho_vac_up) other than rho_vac itself).
-__device__ __forceinline__ int correct_energy_f32(float u[6], float rho_vac_up, double rho_vac) {
+// The two branches separately, for callers that batch cells: whether u takes the vacuum
+// branch, the dense branch's rho eps, and the vacuum branch applied to u.
+__device__ __forceinline__ bool vacuum_cell_f32(const float u[6], float rho_vac_up) {
   const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-  if (u[0] < rho_vac_up && m2 > 0.f) {
-    double d[6] = {u[0], u[1], u[2], u[3], u[4], u[5]};
-    energy_correction(d, rho_vac);
-    u[1] = (float)d[1];
-    u[2] = (float)d[2];
-    u[3] = (float)d[3];
-    u[5] = (float)d[5];
+  return u[0] < rho_vac_up && m2 > 0.f;
+}
+__device__ __forceinline__ float dense_eps_f32(const float u[6]) {
+  const float e = internal_energy_ff(u[0], u[1], u[2], u[3], u[4]);
+  return e > 0.f ? e : u[5];
+}
+__device__ __forceinline__ void vacuum_correct_f32(float u[6], double rho_vac) {
+  double d[6] = {u[0], u[1], u[2], u[3], u[4], u[5]};
+  energy_correction(d, rho_vac);
+  u[1] = (float)d[1];
+  u[2] = (float)d[2];
+  u[3] = (float)d[3];
+  u[5] = (float)d[5];
+}
+__device__ __forceinline__ int correct_energy_f32(float u[6], float rho_vac_up, double rho_vac) {
+  if (vacuum_cell_f32(u, rho_vac_up)) {
+    vacuum_correct_f32(u, rho_vac);
     return 1;
   }
-  const float e = internal_energy_ff(u[0], u[1], u[2], u[3], u[4]);
-  if (e > 0.f) u[5] = e;
+  u[5] = dense_eps_f32(u);
   return 0;
 }
 template <>
