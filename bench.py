@@ -7,8 +7,16 @@ in libppml.so through its C ABI.  The state (6 x 67 MB in FP32) is far larger th
 so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ppml|reference]
+                       [--all-configs] [--cpu-table]
 Under torchrun with N > 1 each rank advances its own replica (the grid is not split
 across GPUs); value = all ranks' cell-updates / max-over-ranks time.
+
+The line's "configs" object times the other workloads on the GPU beside the headline: the
+1D Sod run to t = 0.2 (launch-bound) and the planar Sod 128^3 in FP32 and FP64, and with
+--all-configs also the 512^3 galactic disk (hydro steps with gravity; the Poisson solve
+between them untimed).  --cpu-table instead times the FP64 oracle, as it stands, on a
+bounded sample of every workload with one thread and with all host cores (no GPU use) and
+prints that table as its one JSON line.
 """
 from __future__ import annotations
 
@@ -145,6 +153,214 @@ def cpu_baseline(workload_steps=1, max_seconds=30.0):
     return pb.cells * steps / el / 1e6, cores, f"{steps} oracle step(s) of the 256^3 point blast from t=0", el
 
 
+def _oracle_grid(pb):
+    import oracle
+    return oracle.Grid(pb.n, pb.h, pb.gamma, pb.bc, pb.cfl, rho_mean=oracle.mean_density(pb.u))
+
+
+def _oracle_steps(pb, max_steps, max_seconds, phi=None):
+    """Oracle steps of pb from t = 0 until max_steps or max_seconds (at least one); the
+    CFL step of each comes from the previous step's diagnostics.  Returns (steps, s)."""
+    import oracle
+    g = _oracle_grid(pb)
+    u = pb.u
+    dt = oracle.cfl_dt(g, u)
+    steps, el = 0, 0.0
+    while steps < max_steps and (steps == 0 or el < max_seconds):
+        t0 = time.perf_counter()
+        u, dg = oracle.step(g, u, dt, phi=phi)
+        el += time.perf_counter() - t0
+        dt = dg["dt_cfl"]
+        steps += 1
+    return steps, el
+
+
+def oracle_config_table(disk_n, max_seconds=15.0):
+    """The FP64 oracle (as it stands) on a bounded sample of each workload, with the
+    OpenMP thread count of this process.  Returns {workload: {mcups, seconds, sample}}."""
+    import oracle
+    from oracle import exact
+    from paper_1607_01105_gb300 import inputs
+    out = {}
+
+    def put(name, updates, el, sample):
+        out[name] = {"mcups": updates / el / 1e6, "seconds": el, "sample": sample}
+
+    pb = inputs.sod_1d(256)
+    t0 = time.perf_counter()
+    _, _, steps, _ = oracle.run(_oracle_grid(pb), pb.u, pb.t_end)
+    put("sod_1d_256", pb.cells * steps, time.perf_counter() - t0,
+        f"full run to t = {pb.t_end}: {steps} steps")
+    for name, pb in (("planar_sod_128", inputs.planar_sod_3d(128)),
+                     ("point_blast_256", inputs.point_blast_3d(256))):
+        steps, el = _oracle_steps(pb, 10, max_seconds)
+        put(name, pb.cells * steps, el, f"{steps} step(s) from t = 0")
+    bb = inputs.batched_riemann(max_speed=exact.riemann_max_speed)
+    updates, el, done = 0.0, 0.0, 0
+    for i in range(bb.ncells.size):
+        n = int(bb.ncells[i])
+        sl = slice(bb.offsets[i], bb.offsets[i + 1])
+        z = np.zeros(n)
+        u = [bb.u[0][sl], bb.u[1][sl], z, z, bb.u[2][sl], bb.u[3][sl]]
+        g = oracle.Grid((n, 1, 1), (float(bb.h[i]), 1.0, 1.0), bb.gamma, (0,) * 6, bb.cfl,
+                        rho_mean=float(np.mean(bb.u[0][sl])))
+        t0 = time.perf_counter()
+        _, _, steps, _ = oracle.run(g, [x[None, None, :] for x in u], float(bb.t_end[i]))
+        el += time.perf_counter() - t0
+        updates += n * steps
+        done += 1
+        if el > max_seconds:
+            break
+    put("batched_riemann_512", updates, el,
+        f"instances 0..{done - 1} of the 512 (in generator order), each run to its end time")
+    pb = inputs.galactic_disk(n=disk_n)
+    steps, el = _oracle_steps(pb, 2, max_seconds, phi=pb.extra["phi_halo"])
+    put("galactic_disk", pb.cells * steps, el,
+        f"{disk_n}^3 disk, {steps} hydro step(s) with the fixed halo potential")
+    return out
+
+
+def cpu_table(args):
+    """Oracle timings of every workload with 1 thread and with all host cores, each in a
+    fresh process (OMP_NUM_THREADS fixed at its start); one JSON line."""
+    cores = os.cpu_count() or 1
+    table = {}
+    for threads, disk_n in ((1, 128), (cores, 512)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-table-worker",
+                            "--disk-n", str(disk_n)], env=env, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle table worker ({threads} threads) failed:\n{r.stderr[-2000:]}")
+        table[str(threads)] = json.loads(r.stdout.strip().splitlines()[-1])
+    print(json.dumps({"cpu_table": table, "kind": "oracle", "unit": "Mcell-updates/s",
+                      "cores": cores, "data": "synthetic"}), flush=True)
+    return 0
+
+
+def gpu_configs(args, dev, stream, barrier, with_disk):
+    """GPU timings of the other workloads through the same C ABI (CUDA events on the
+    launching stream): the 1D Sod 256 run to t = 0.2 (the steps of the full run, counted
+    in an untimed run first, then launched back to back from t = 0 on a fresh grid), the
+    planar Sod 128^3 (warm-up, then timed steps) and optionally the 512^3 galactic disk
+    (hydro steps with the periodic self-gravity solve plus the halo potential; each
+    Poisson solve outside the timed events)."""
+    import torch
+    from paper_1607_01105_gb300 import inputs, ppml
+    out = {}
+    kinds = ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64"))
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    pb = inputs.sod_1d(256)
+    res = {}
+    for dtype, name in kinds:
+        u = ppml.to_device(pb.u, dtype)
+        v = [torch.empty_like(x) for x in u]
+        g = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u, t_end=pb.t_end)
+        uu, vv, steps = [x.clone() for x in u], v, 0
+        while g.diag(raise_nonphysical=False)["dt_next"] > 0.0 and steps < 100000:
+            g.step(uu, vv, 0.0)
+            uu, vv = vv, uu
+            steps += 1
+        g.close()
+        g = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u, t_end=pb.t_end)
+        uu, vv = [x.clone() for x in u], v
+        e0, e1 = events()
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            g.step(uu, vv, 0.0)
+            uu, vv = vv, uu
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        t = g.diag(raise_nonphysical=False)["t"]
+        g.close()
+        res[name] = {"value": pb.cells * steps / (ms * 1e-3) / 1e6, "ms": ms, "steps": steps,
+                     "t": t}
+    out["sod_1d_256"] = dict(res, unit="Mcell-updates/s",
+                             workload="Sod (Table 2 row 1), 256 cells, CFL 0.4, outflow, run to "
+                                      "t = 0.2, through the grid path (three launches per step)")
+    # the same run as a batch of one instance: the whole run in one persistent launch
+    res = {}
+    for dtype, name in kinds:
+        st = [torch.as_tensor(np.asarray(pb.u[f]).ravel()).to(dev, ppml.torch_dtype(dtype))
+              for f in (0, 1, 4, 5)]
+        b = ppml.Batch([pb.cells], [pb.h[0]], [pb.t_end], pb.gamma, pb.cfl, dtype)
+        e0, e1 = events()
+        barrier()
+        e0.record(stream)
+        b.step(st, 1 << 30)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        t, steps = b.status()
+        b.close()
+        res[name] = {"value": pb.cells * steps[0] / (ms * 1e-3) / 1e6, "ms": ms,
+                     "steps": int(steps[0]), "t": float(t[0])}
+    out["sod_1d_256_batch"] = dict(res, unit="Mcell-updates/s",
+                                   workload="the same Sod run as a batch of one instance "
+                                            "(ppml_batch_step: one launch for the whole run)")
+    pb = inputs.planar_sod_3d(128)
+    res = {}
+    for dtype, name in kinds:
+        steps = args.steps if dtype == ppml.PPML_F32 else max(3, args.steps // 10)
+        u = ppml.to_device(pb.u, dtype)
+        v = [torch.empty_like(x) for x in u]
+        g = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u)
+        for _ in range(args.warmup):
+            g.step(u, v, 0.0)
+            u, v = v, u
+        e0, e1 = events()
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            g.step(u, v, 0.0)
+            u, v = v, u
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        g.close()
+        res[name] = {"value": pb.cells * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                     "steps": steps}
+    out["planar_sod_128"] = dict(res, unit="Mcell-updates/s",
+                                 workload="planar Sod 128^3, split on x = 0.5, outflow in x, "
+                                          "periodic in y and z, CFL 0.2")
+    if with_disk:
+        pb = inputs.galactic_disk(n=512)
+        dtype = ppml.PPML_F32
+        u = ppml.to_device(pb.u, dtype)
+        v = [torch.empty_like(x) for x in u]
+        g = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u)
+        halo = torch.as_tensor(pb.extra["phi_halo"].ravel()).to(dev, torch.float32)
+        phi = torch.empty_like(u[0])
+        ms, steps = 0.0, args.steps
+        for k in range(args.warmup + steps):
+            g.poisson_periodic(u[0], phi, 1.0)
+            phi.add_(halo)
+            e0, e1 = events()
+            barrier()
+            e0.record(stream)
+            g.step_phi(u, v, phi, 0.0)
+            e1.record(stream)
+            barrier()
+            if k >= args.warmup:
+                ms += e0.elapsed_time(e1)
+            u, v = v, u
+        g.close()
+        out["galactic_disk_512"] = {
+            "f32": {"value": pb.cells * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                    "steps": steps},
+            "unit": "Mcell-updates/s",
+            "workload": "galactic disk 512^3 (exponential disk in a fixed halo, G = 1), FP32; "
+                        "hydro steps with gravity, each step timed alone, the Poisson solve "
+                        "before it untimed"}
+        del u, v, phi, halo
+        torch.cuda.empty_cache()
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -183,9 +399,18 @@ def main():
     ap.add_argument("--impl", default="ppml", choices=["ppml", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    ap.add_argument("--all-configs", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true")
+    ap.add_argument("--cpu-table-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--disk-n", type=int, default=512, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.cpu_table_worker:
+        print(json.dumps(oracle_config_table(args.disk_n)), flush=True)
+        return 0
+    if args.cpu_table:
+        return cpu_table(args)
 
     import torch
     import torch.distributed as dist
@@ -356,6 +581,8 @@ def main():
         del u, v
         torch.cuda.empty_cache()
 
+    configs = gpu_configs(args, dev, stream, barrier, args.all_configs)
+
     if rank == 0:
         peak, peak_kind = load_peaks()
         r32, r64 = results["f32"], results["f64"]
@@ -422,6 +649,7 @@ def main():
                                 "(at most 4000 steps; t reached is given)"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "configs": configs,
             "gpu_launches": 3 * r32["steps"],
             "clocks": r32["clocks"],
             "clocks_fp64": r64["clocks"],

@@ -260,6 +260,32 @@ def test_config1_sod_fp64_and_fp32():
         assert d32["sums"][f] == pytest.approx(dgo["sums"][f], rel=1e-6)
 
 
+def test_config1_sod_as_one_instance_batch():
+    """The same Sod run through the batch path (one instance, one launch for the whole
+    run): FP64 bit for bit and with the oracle's step count, FP32 within 1e-4 (rho,
+    rho eps) and at most one step apart."""
+    pb = inputs.sod_1d(256)
+    g = oracle_grid(pb)
+    ref, t, steps_o, dgo = oracle.run(g, pb.u, pb.t_end)
+    for dtype in (F64, F32):
+        st = [torch.as_tensor(np.asarray(pb.u[f]).ravel()).to("cuda", ppml.torch_dtype(dtype))
+              for f in (0, 1, 4, 5)]
+        b = ppml.Batch([pb.cells], [pb.h[0]], [pb.t_end], pb.gamma, pb.cfl, dtype)
+        assert b.step(st, 1 << 30, sync=True) == 1
+        tt, steps = b.status()
+        assert tt[0] == pytest.approx(0.2, rel=1e-14)
+        got = [x.double().cpu().numpy() for x in st]
+        if dtype == F64:
+            assert steps[0] == steps_o
+            for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+                assert np.array_equal(got[k], ref[f].ravel()), f
+        else:
+            assert abs(steps[0] - steps_o) <= 1
+            assert rel_l1(got[0], ref[0].ravel()) <= 1e-4
+            assert rel_l1(got[3], ref[5].ravel()) <= 1e-4
+        b.close()
+
+
 def test_two_blast_waves_reflecting_fp64_fp32():
     """Two interacting blast waves (2400 cells, reflecting walls, about 10^4 steps to
     t = 0.038) with the device-resident step: FP64 identical to the oracle run, FP32 within
