@@ -582,6 +582,9 @@ def main():
         torch.cuda.empty_cache()
 
     configs = gpu_configs(args, dev, stream, barrier, args.all_configs)
+    # measured FMA throughput of the device (the arithmetic roofline denominators)
+    fma_peak = {"f32": ppml.fma_peak(ppml.PPML_F32, 200000, stream=stream),
+                "f64": ppml.fma_peak(ppml.PPML_F64, 4000, stream=stream)}
 
     if rank == 0:
         peak, peak_kind = load_peaks()
@@ -627,7 +630,19 @@ def main():
                                  "algorithmic_bytes_per_cell": BYTES_EUL[4] + BYTES_LAG[4],
                                  "step_frac": step_bytes / (r32["ms"] / r32["steps"] * 1e-3) / 1e9 / peak}},
             "fp64": {"value": v64, "unit": "Mcell-updates/s", "ms_per_step": r64["ms"] / r64["steps"],
-                     "steps": r64["steps"], "kernel_ms": r64["kernel_ms"]},
+                     "steps": r64["steps"], "kernel_ms": r64["kernel_ms"],
+                     "roofline": {"bound": "alu", "kernel": "lagrangian_tile<double>",
+                                  "achieved": OPS_LAG * cells / (r64["kernel_ms"][1] * 1e-3) / 1e12,
+                                  "peak": fma_peak["f64"] / 1e12, "unit": "TFLOP/s",
+                                  "frac": OPS_LAG * cells / (r64["kernel_ms"][1] * 1e-3) / fma_peak["f64"],
+                                  "peak_kind": "measured FP64 FMA throughput (ppml_fma_peak), "
+                                               "an FMA counted once",
+                                  "algorithmic_ops_per_cell": OPS_LAG,
+                                  "note": "IEEE division and square root are sequences of "
+                                          "several FP64 instructions but count once"}},
+            "fma_peak_measured": {"f32_tfma_s": fma_peak["f32"] / 1e12,
+                                  "f64_tfma_s": fma_peak["f64"] / 1e12,
+                                  "lagrangian_f32_frac_of_measured": lag_ops * 1e12 / fma_peak["f32"]},
             "batch_riemann": {"value": results["batch"]["updates"] / (results["batch"]["ms"] * 1e-3) / 1e6,
                               "unit": "Mcell-updates/s", "ms": results["batch"]["ms"],
                               "instances": results["batch"]["instances"],

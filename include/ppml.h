@@ -270,6 +270,15 @@ int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stre
 
 int ppml_batch_free(ppml_batch* b);
 
+/* ---------------------------------------------------------------- measurement aid
+ * Fused multiply-add throughput of the current device for dtype PPML_F32 or PPML_F64
+ * (the paper has no counterpart: the denominator of the arithmetic rooflines).  Launches a
+ * kernel of 8 CTAs of 256 threads per SM, each thread running 8 independent FMA chains for
+ * `iters` (>= 1) iterations without memory traffic, once untimed and once timed with CUDA
+ * events on `stream`; writes the FMAs per second of the timed launch (an FMA counted once)
+ * to *fma_per_s.  Allocates and frees one scratch array; synchronizes the stream. */
+int ppml_fma_peak(int dtype, int iters, double* fma_per_s, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* ppml_last_error(void);
 

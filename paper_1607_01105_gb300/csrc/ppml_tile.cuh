@@ -615,23 +615,40 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   unsigned long long nvac = 0, nbad = 0;
   const float rho_vac_up = __double2float_ru(A.rho_vac);
   // groups of FB cells: all loads of a group are issued before its first store
-  constexpr int FB = 2;
+  constexpr int FB = 4;
 #pragma unroll 1
   for (int c0 = 0; c0 < nvalid_z; c0 += FB) {
     T u[FB][6];
 #pragma unroll
     for (int q = 0; q < FB; q++)
-      if (c0 + q < nvalid_z)
 #pragma unroll
-        for (int f = 0; f < 6; f++) u[q][f] = A.out[f][zline0 + g.nxy * (c0 + q)];
+      for (int f = 0; f < 6; f++)
+        u[q][f] = c0 + q < nvalid_z ? A.out[f][zline0 + g.nxy * (c0 + q)] : T(1);
+    if constexpr (sizeof(T) == 4) {
+      // the dense branch for every cell of the group without control flow (so that the
+      // cells' chains interleave), then the rare vacuum cells on their stored values
+      bool vac[FB], any_vac = false;
+#pragma unroll
+      for (int q = 0; q < FB; q++) {
+        vac[q] = c0 + q < nvalid_z && vacuum_cell_f32(u[q], rho_vac_up);
+        any_vac |= vac[q];
+        const float e = dense_eps_f32(u[q]);
+        u[q][5] = vac[q] ? u[q][5] : e;
+      }
+      if (any_vac) {
+#pragma unroll
+        for (int q = 0; q < FB; q++)
+          if (vac[q]) {
+            vacuum_correct_f32(u[q], A.rho_vac);
+            nvac++;
+          }
+      }
+    }
 #pragma unroll
     for (int q = 0; q < FB; q++) {
       if (c0 + q >= nvalid_z) break;
       const long long idx = zline0 + g.nxy * (c0 + q);
-      if constexpr (sizeof(T) == 4)
-        nvac += correct_energy_f32(u[q], rho_vac_up, A.rho_vac);
-      else
-        nvac += correct_energy<T>(u[q], A.rho_vac);
+      if constexpr (sizeof(T) != 4) nvac += correct_energy<T>(u[q], A.rho_vac);
       A.out[1][idx] = u[q][1];
       A.out[2][idx] = u[q][2];
       A.out[3][idx] = u[q][3];

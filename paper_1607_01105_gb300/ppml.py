@@ -29,7 +29,7 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
-            "ppml_batch_set_threads", "ppml_fourier_amplitudes")
+            "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak")
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -81,6 +81,7 @@ _lib.ppml_fourier_amplitudes.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+_lib.ppml_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
 
 
 class PPMLError(RuntimeError):
@@ -335,6 +336,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak(dtype: int, iters: int, stream=None) -> float:
+    """Measured FMAs per second of the device for PPML_F32 or PPML_F64 (ppml_fma_peak)."""
+    out = ctypes.c_double()
+    _check(_lib.ppml_fma_peak(int(dtype), int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def to_device(u, dtype: int, device="cuda"):

@@ -800,3 +800,17 @@ def test_cuda_graph_replay_equals_eager():
     for x, y in zip(a, ea):
         assert torch.equal(x, y)
     assert gg.diag()["steps"] == 4
+
+
+def test_fma_peak_measurement():
+    """The FMA-throughput probe behind the arithmetic rooflines: finite, positive, FP32
+    within the range a 152-SM part at up to 2.1 GHz allows (128 FP32 lanes per SM, one FMA
+    per lane per clock), FP64 below FP32; invalid arguments are rejected."""
+    f32 = ppml.fma_peak(ppml.PPML_F32, 20000)
+    f64 = ppml.fma_peak(ppml.PPML_F64, 500)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0.25 * sms * 128 * 1.0e9 < f32 <= 1.05 * sms * 128 * 2.1e9
+    assert 0.0 < f64 < f32
+    for bad in ((ppml.PPML_F32, 0), (7, 10)):
+        with pytest.raises(ppml.PPMLError):
+            ppml.fma_peak(*bad)
