@@ -49,7 +49,7 @@ OPS_LAG = 18 * 62 + 57 + 30 + 12 + 42
 OPS_EUL = 3 * (84 + 15 + 32 + 9 + 8 + 1) + 6
 # DRAM bytes per Lagrangian launch measured by ncu (dram__bytes_read + write) on the
 # 160^3 point blast, per cell (scaled to the workload's cells); see profiles/.
-NCU_LAG_DRAM_BYTES_PER_CELL = (101.341440e6 + 62.453504e6) / 160 ** 3
+NCU_LAG_DRAM_BYTES_PER_CELL = (101.166336e6 + 65.506560e6) / 160 ** 3
 SMS, FP32_LANES = 152, 128
 
 
