@@ -238,10 +238,12 @@ typedef struct ppml_batch ppml_batch;
 
 /* ncells[n_inst] (each >= 4), h[n_inst] (> 0), t_end[n_inst] (> 0) are host arrays;
  * they are copied.  vacuum_frac <= 0 selects 1e-5 (reference: each instance's own mean
- * initial density, computed at the first ppml_batch_step).  The largest instance (n cells)
- * must fit in one CTA's shared memory: 4 (n + 6) + 4 (n + 1) floats in FP32, 4 (n + 6) +
- * 2 (n + 1) doubles in FP64, plus 1 KB, within the device's opt-in limit (on GB300 up to
- * 7228 FP32 or 4817 FP64 cells); else PPML_E_INVAL. */
+ * initial density, computed at the first ppml_batch_step).  Every instance must fit in
+ * one CTA's shared memory: a one-CTA instance of n cells needs 4 (n + 6) + 4 (n + 1) floats
+ * in FP32, 4 (n + 6) + 2 (n + 1) doubles in FP64, plus 1 KB, within the device's opt-in
+ * limit (on GB300 up to 7228 FP32 or 4817 FP64 cells); a paired instance (see
+ * ppml_batch_set_split) needs the same for m = ceil(n / 2) with 4 (m + 12) + 4 (m + 8)
+ * floats or 4 (m + 12) + 2 (m + 8) doubles; else PPML_E_INVAL. */
 int ppml_batch_init(int n_inst, const int* ncells, const double* h, const double* t_end,
                     double gamma, double cfl, double vacuum_frac, int dtype, ppml_batch** out);
 
@@ -264,6 +266,18 @@ int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* don
 int ppml_batch_set_threads(ppml_batch* b, int threads);
 int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps, int* threads_out,
                     double ms_out[3], void* stream);
+
+/* Instances of at least min_cells cells (min_cells >= 64) are each split over the two CTAs
+ * of one thread-block cluster, half of the cells each; the two exchange a 6-cell halo and
+ * their CFL maxima through distributed shared memory once per step, so the longest runs
+ * use two SMs.  The launch is then one grid of two-CTA clusters, each taking a split
+ * instance or two whole instances of neighbouring sizes (one per CTA), largest first.
+ * min_cells = 0: no split (one CTA per instance).  ppml_batch_init selects
+ * max(256, ceil(7 largest / 8)).  Results do not depend on the split (the same operations
+ * per cell, in the same order); the work plan is rebuilt (host to device copy).
+ * PPML_E_INVAL for 0 < min_cells < 64 or if an instance would not fit (the previous
+ * split is kept). */
+int ppml_batch_set_split(ppml_batch* b, int min_cells);
 
 /* Per-instance time reached and steps taken (host arrays of n_inst).  Synchronizes. */
 int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream);

@@ -16,27 +16,107 @@
 using namespace ppml;
 
 struct ppml_batch {
-  int n_inst, dtype, nmax;
+  int n_inst, dtype;
   long long total;
   double gamma, cfl;
+  std::vector<int> ncells;
   InstDev* inst;
-  int* order;
-  size_t smem;
+  int* order;   // one-CTA launch: the instances, largest first
+  int2* items;  // cluster launch: the work items, largest first
   int threads;  // CTA size of the launch: 256, 512 or 1024 (ppml_batch_tune / _set_threads)
+  int split_min;         // instances of at least this many cells are split over a CTA pair
+  int n_items, n_split;  // cluster launch: items, of which split instances (0: one-CTA launch)
+  int nlmax, nmax;       // largest half of a split instance; largest one-CTA instance
+  size_t smem;
 };
 
 namespace {
 constexpr int kBatchSizes[3] = {256, 512, 1024};
+constexpr int kSplitFloor = 64;  // smallest instance a CTA pair may take
+
+// Shared memory of one CTA: four fields padded by `pad` on each side and `nface` face
+// arrays of `faces` values.
+size_t batch_smem(int cells, int pad, int nface, int faces, size_t elt) {
+  return (4 * (size_t)(cells + 2 * pad) + (size_t)nface * faces) * elt;
+}
+
+// Work plan for b->split_min: with no instance split, one CTA per instance (largest
+// first); else one cluster of two CTAs per work item -- a split instance, or two one-CTA
+// instances of neighbouring sizes -- ordered largest first by the size of the item's
+// largest instance.  Sizes the launch's shared memory.
+int plan_batch(ppml_batch* b) {
+  const size_t elt = b->dtype == PPML_F64 ? 8 : 4;
+  const int nface = b->dtype == PPML_F64 ? kBatchFaceArrays<double> : kBatchFaceArrays<float>;
+  std::vector<int> split, rest;
+  for (int i = 0; i < b->n_inst; i++)
+    (b->split_min > 0 && b->ncells[i] >= b->split_min ? split : rest).push_back(i);
+  auto by_size = [&](int x, int y) { return b->ncells[x] > b->ncells[y]; };
+  std::stable_sort(split.begin(), split.end(), by_size);
+  std::stable_sort(rest.begin(), rest.end(), by_size);
+  int nlmax = 0, nmax = 0;
+  for (int i : split) nlmax = std::max(nlmax, b->ncells[i] - b->ncells[i] / 2);
+  for (int i : rest) nmax = std::max(nmax, b->ncells[i]);
+  const size_t smem_split = split.empty() ? 0 : batch_smem(nlmax, kPairHalo, nface, nlmax + 8, elt);
+  const size_t smem_one = rest.empty() ? 0 : batch_smem(nmax, kBatchGhost, nface, nmax + 1, elt);
+  const size_t smem = std::max(smem_split, smem_one);
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem + 1024 > (size_t)maxsm)
+    return ppml_fail(PPML_E_INVAL,
+                     "largest instance needs %zu bytes of shared memory (> %d): %d cells on one "
+                     "CTA, %d cells per CTA of a split one",
+                     smem, maxsm, nmax, nlmax);
+  std::vector<int2> items;
+  if (!split.empty()) {
+    std::vector<std::pair<int, int2>> keyed;  // (largest size, item)
+    for (int i : split) keyed.push_back({b->ncells[i], make_int2(i, kItemSplit)});
+    for (size_t k = 0; k < rest.size(); k += 2)
+      keyed.push_back({b->ncells[rest[k]], make_int2(rest[k], k + 1 < rest.size() ? rest[k + 1] : -1)});
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) {
+                       return x.first > y.first;
+                     });
+    for (auto& x : keyed) items.push_back(x.second);
+    if (cudaMemcpy(b->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return ppml_fail(PPML_E_CUDA, "batch items copy: %s", cudaGetErrorString(cudaGetLastError()));
+  } else if (cudaMemcpy(b->order, rest.data(), sizeof(int) * rest.size(),
+                        cudaMemcpyHostToDevice) != cudaSuccess) {
+    return ppml_fail(PPML_E_CUDA, "batch order copy: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  b->n_items = (int)items.size();
+  b->n_split = (int)split.size();
+  b->nlmax = nlmax;
+  b->nmax = nmax;
+  b->smem = smem;
+  return PPML_OK;
+}
+
+template <typename T>
+int launch_typed_t(ppml_batch* b, void* const state[4], InstDev* inst, int max_steps,
+                   int threads, cudaStream_t st) {
+  T* f[4] = {(T*)state[0], (T*)state[1], (T*)state[2], (T*)state[3]};
+  int rc = launch_batch_vacuum<T>(f[0], inst, b->n_inst, st);
+  if (rc) return rc;
+  if (b->n_items == 0)
+    return launch_batch<T>(f[0], f[1], f[2], f[3], inst, b->order, b->gamma, b->cfl, max_steps,
+                           b->nmax, b->n_inst, b->smem, threads, st);
+  return launch_batch_cluster<T>(f[0], f[1], f[2], f[3], inst, b->items, b->gamma, b->cfl,
+                                 max_steps, b->nlmax, b->nmax, b->n_items, b->smem, threads, st);
+}
+
+void release_batch(ppml_batch* b) {
+  if (b->inst) cudaFree(b->inst);
+  if (b->order) cudaFree(b->order);
+  if (b->items) cudaFree(b->items);
+  delete b;
+}
 
 int launch_typed(ppml_batch* b, void* const state[4], InstDev* inst, int max_steps, int threads,
                  cudaStream_t st) {
-  return b->dtype == PPML_F64
-             ? launch_batch<double>((double*)state[0], (double*)state[1], (double*)state[2],
-                                    (double*)state[3], inst, b->order, b->gamma, b->cfl,
-                                    max_steps, b->nmax, b->n_inst, b->smem, threads, st)
-             : launch_batch<float>((float*)state[0], (float*)state[1], (float*)state[2],
-                                   (float*)state[3], inst, b->order, b->gamma, b->cfl, max_steps,
-                                   b->nmax, b->n_inst, b->smem, threads, st);
+  return b->dtype == PPML_F64 ? launch_typed_t<double>(b, state, inst, max_steps, threads, st)
+                              : launch_typed_t<float>(b, state, inst, max_steps, threads, st);
 }
 
 int check_state(void* const state[4]) {
@@ -61,7 +141,6 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
   if (!(cfl > 0.0 && cfl < 1.0)) return ppml_fail(PPML_E_INVAL, "cfl = %g not in (0,1)", cfl);
   if (dtype != PPML_F32 && dtype != PPML_F64) return ppml_fail(PPML_E_INVAL, "bad dtype %d", dtype);
   if (!(vacuum_frac > 0.0)) vacuum_frac = 1e-5;
-  const size_t elt = dtype == PPML_F64 ? 8 : 4;
   std::vector<InstDev> hi(n_inst);
   long long off = 0;
   int nmax = 0;
@@ -81,37 +160,32 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
     off += ncells[i];
     nmax = std::max(nmax, ncells[i]);
   }
-  const int nface = dtype == PPML_F64 ? kBatchFaceArrays<double> : kBatchFaceArrays<float>;
-  const size_t smem = (4 * (size_t)(nmax + 2 * kBatchGhost) + nface * (size_t)(nmax + 1)) * elt;
-  int dev = 0, maxsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem + 1024 > (size_t)maxsm)
-    return ppml_fail(PPML_E_INVAL, "largest instance (%d cells) needs %zu bytes of shared memory (> %d)",
-                     nmax, smem, maxsm);
-  // largest work first (work ~ n^2: cells x steps), so long instances start early
-  std::vector<int> ord(n_inst);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ncells[a] > ncells[b]; });
   ppml_batch* b = new (std::nothrow) ppml_batch();
   if (!b) return ppml_fail(PPML_E_NOMEM, "host allocation failed");
   b->n_inst = n_inst;
   b->dtype = dtype;
-  b->nmax = nmax;
   b->total = off;
   b->gamma = gamma;
   b->cfl = cfl;
-  b->smem = smem;
+  b->ncells.assign(ncells, ncells + n_inst);
   b->threads = 512;
+  // default split: the instances within 1/8 of the largest size (and of at least 256
+  // cells) take a CTA pair, so the longest runs are not left to one SM each
+  b->split_min = std::max(256, (7 * nmax + 7) / 8);
+  int rc = PPML_OK;
   if (cudaMalloc(&b->inst, sizeof(InstDev) * n_inst) != cudaSuccess ||
-      cudaMalloc(&b->order, sizeof(int) * n_inst) != cudaSuccess) {
-    ppml_batch_free(b);
-    return ppml_fail(PPML_E_NOMEM, "cudaMalloc of batch metadata failed");
-  }
-  if (cudaMemcpy(b->inst, hi.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->order, ord.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice) != cudaSuccess) {
-    ppml_batch_free(b);
-    return ppml_fail(PPML_E_CUDA, "batch init copy: %s", cudaGetErrorString(cudaGetLastError()));
+      cudaMalloc(&b->order, sizeof(int) * n_inst) != cudaSuccess ||
+      cudaMalloc(&b->items, sizeof(int2) * n_inst) != cudaSuccess)
+    rc = ppml_fail(PPML_E_NOMEM, "cudaMalloc of batch metadata failed");
+  else if (cudaMemcpy(b->inst, hi.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice) !=
+           cudaSuccess)
+    rc = ppml_fail(PPML_E_CUDA, "batch init copy: %s", cudaGetErrorString(cudaGetLastError()));
+  else
+    rc = plan_batch(b);
+  if (rc) {  // release without clearing the failure's message
+    cudaGetLastError();
+    release_batch(b);
+    return rc;
   }
   *out = b;
   return PPML_OK;
@@ -149,6 +223,21 @@ extern "C" int ppml_batch_set_threads(ppml_batch* b, int threads) {
       return PPML_OK;
     }
   return ppml_fail(PPML_E_INVAL, "threads = %d is not 256, 512 or 1024", threads);
+}
+
+extern "C" int ppml_batch_set_split(ppml_batch* b, int min_cells) {
+  ppml_clear_error();
+  if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
+  if (min_cells != 0 && min_cells < kSplitFloor)
+    return ppml_fail(PPML_E_INVAL, "min_cells = %d: 0 (no pairs) or >= %d", min_cells, kSplitFloor);
+  const int old = b->split_min;
+  b->split_min = min_cells;
+  const int rc = plan_batch(b);
+  if (rc) {
+    b->split_min = old;
+    plan_batch(b);
+  }
+  return rc;
 }
 
 extern "C" int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps,
@@ -233,8 +322,6 @@ extern "C" int ppml_batch_free(ppml_batch* b) {
   ppml_clear_error();
   if (!b) return PPML_OK;
   cudaDeviceSynchronize();
-  if (b->inst) cudaFree(b->inst);
-  if (b->order) cudaFree(b->order);
-  delete b;
+  release_batch(b);
   return PPML_OK;
 }

@@ -9,6 +9,8 @@
 // instance) is a template parameter; the host picks it by timing the candidates on the
 // actual batch (ppml_batch_tune).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "ppml_device.cuh"
 
 namespace ppml {
@@ -19,6 +21,16 @@ constexpr int kBatchGhost = 3;
 // FP64 takes the fields in turn through two, so that 4096-cell instances fit in 227 KB.
 template <typename T>
 constexpr int kBatchFaceArrays = sizeof(T) == 4 ? 4 : 2;
+// An instance split over a CTA pair: halo cells facing the partner, and the exchange slot
+// (the kPairHalo edge cells of the four fields, then the two CFL maxima).
+constexpr int kPairHalo = 6;
+constexpr int kPairSlot = 4 * kPairHalo + 2;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  return cooperative_groups::this_cluster().block_rank();
+}
+// barrier of all threads of the cluster (release / acquire of the cluster's shared memory)
+__device__ __forceinline__ void cluster_sync() { cooperative_groups::this_cluster().sync(); }
 
 struct InstDev {
   long long off;  // first cell in the packed arrays
@@ -167,76 +179,95 @@ __device__ __forceinline__ T vel_of(T m, T r) {
     return m / r;
 }
 
-// CFL step of the CTA's instance (Sec. 1.1) from the per-thread maxima a = max|v|,
-// b = max c: warp maxima, then warp 0 folds the warps' (maxima in the state's precision;
-// a maximum is exact in any).  Thread 0 alone keeps the instance's time (t, steps, done):
-// it stops the CTA once t has reached t_end, else forms tau clipped to the remaining time
-// and advances t.  FP64 forms tau = cfl h / (a + b) and tau / h as the checker does; FP32
-// forms tau / h = cfl / (a + b) in FP32 and tau = (tau / h) h in FP64 (both divisions of
-// the FP64 form, at the FP64 pipe's latency, would lie on every step's critical path).
-// Returns whether the CTA takes the step (the same in every thread), with th = tau / h
-// and, in FP64, dt = tau.  Two barriers; the caller puts at least one more between two
-// calls, so the next call's writes to sh cannot overtake this call's reads.
+// Thread 0's CFL decision from the instance's maxima A = max|v|, B = max c (Sec. 1.1).
+// Thread 0 alone keeps the instance's time (t, steps, done): it stops once t has reached
+// t_end, else forms tau clipped to the remaining time and advances t.  FP64 forms tau =
+// cfl h / (A + B) and tau / h as the checker does; FP32 forms tau / h = cfl / (A + B) in
+// FP32 and tau = (tau / h) h in FP64 (both divisions of the FP64 form, at the FP64 pipe's
+// latency, would lie on every step's critical path).  Publishes tau (sh[64]), tau / h
+// (sh + 66) and the go flag (sh + 68).
 template <typename T>
-__device__ __forceinline__ bool block_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
-                                               double& dt, T& th) {
+__device__ __forceinline__ void cfl_decide(T A, T B, double cfl, InstDev& I, double* sh) {
+  int go = 0;
+  double d = 0.0;
+  T q = T(0);
+  if (!(I.t >= I.t_end)) {
+    const double rem = I.t_end - I.t;
+    if constexpr (sizeof(T) == 4) {
+      q = (float)cfl / (A + B);
+      d = (double)q * I.h;
+      if (d > rem) {
+        d = rem;
+        q = (float)(rem / I.h);
+      }
+    } else {
+      const double den = A + B;
+      d = cfl * I.h / den;
+      if (d > rem) d = rem;
+      q = d / I.h;
+    }
+    go = d > 0.0;
+  }
+  if (go) {
+    I.t = (I.t + d > I.t_end) ? I.t_end : I.t + d;
+    I.steps += 1;
+  } else {
+    I.done = 1;
+  }
+  sh[64] = d;
+  *reinterpret_cast<T*>(sh + 66) = q;
+  *reinterpret_cast<int*>(sh + 68) = go;
+}
+
+// Warp maxima of (a, b) into sh (as T: slots 0..31 and 32..63); valid after a barrier.
+template <typename T>
+__device__ __forceinline__ void warp_maxima(T a, T b, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
     b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
   }
-  T* shT = reinterpret_cast<T*>(sh);  // 32 + 32 warp maxima
-  int* go_sh = reinterpret_cast<int*>(sh + 68);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    shT[w] = a;
-    shT[32 + w] = b;
+  T* shT = reinterpret_cast<T*>(sh);
+  if ((threadIdx.x & 31) == 0) {
+    shT[threadIdx.x >> 5] = a;
+    shT[32 + (threadIdx.x >> 5)] = b;
   }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = (int)(blockDim.x >> 5);
-    T A = lane < nw ? shT[lane] : T(0), B = lane < nw ? shT[32 + lane] : T(0);
+}
+
+// Warp 0 folds the warp maxima (all 32 lanes take part); lane 0 receives A and B.
+template <typename T>
+__device__ __forceinline__ void fold_maxima(const double* sh, T& A, T& B) {
+  const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  const T* shT = reinterpret_cast<const T*>(sh);
+  A = lane < nw ? shT[lane] : T(0);
+  B = lane < nw ? shT[32 + lane] : T(0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      A = fmax(A, __shfl_down_sync(0xffffffffu, A, o));
-      B = fmax(B, __shfl_down_sync(0xffffffffu, B, o));
-    }
-    if (lane == 0) {
-      int go = 0;
-      double d = 0.0;
-      T q = T(0);
-      if (!(I.t >= I.t_end)) {
-        const double rem = I.t_end - I.t;
-        if constexpr (sizeof(T) == 4) {
-          q = (float)cfl / (A + B);
-          d = (double)q * I.h;
-          if (d > rem) {
-            d = rem;
-            q = (float)(rem / I.h);
-          }
-        } else {
-          const double den = A + B;
-          d = cfl * I.h / den;
-          if (d > rem) d = rem;
-          q = d / I.h;
-        }
-        go = d > 0.0;
-      }
-      if (go) {
-        I.t = (I.t + d > I.t_end) ? I.t_end : I.t + d;
-        I.steps += 1;
-      } else {
-        I.done = 1;
-      }
-      sh[64] = d;
-      *reinterpret_cast<T*>(sh + 66) = q;
-      *go_sh = go;
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    A = fmax(A, __shfl_down_sync(0xffffffffu, A, o));
+    B = fmax(B, __shfl_down_sync(0xffffffffu, B, o));
+  }
+}
+
+// CFL step of the CTA's instance (Sec. 1.1) from the per-thread maxima a = max|v|,
+// b = max c: warp maxima, then warp 0 folds the warps' (maxima in the state's precision;
+// a maximum is exact in any) and thread 0 decides (cfl_decide).  Returns whether the CTA
+// takes the step (the same in every thread), with th = tau / h and dt = tau.  Two
+// barriers; the caller puts at least one more between two calls, so the next call's
+// writes to sh cannot overtake this call's reads.
+template <typename T>
+__device__ __forceinline__ bool block_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
+                                               double& dt, T& th) {
+  warp_maxima<T>(a, b, sh);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T A, B;
+    fold_maxima<T>(sh, A, B);
+    if (threadIdx.x == 0) cfl_decide<T>(A, B, cfl, I, sh);
   }
   __syncthreads();
   dt = sh[64];
   th = *reinterpret_cast<const T*>(sh + 66);
-  return *go_sh != 0;
+  return *reinterpret_cast<const int*>(sh + 68) != 0;
 }
 
 
@@ -263,52 +294,107 @@ __global__ void __launch_bounds__(256) batch_vacuum_kernel(const T* __restrict__
   }
 }
 
-template <typename T, int NTHREADS>
-__global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rho,
-                                                              T* __restrict__ g_m,
-                                                              T* __restrict__ g_en,
-                                                              T* __restrict__ g_ei,
-                                                              InstDev* __restrict__ inst,
-                                                              const int* __restrict__ order,
-                                                              double gamma_d, double cfl,
-                                                              int max_steps, int nmax) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[80];
-  const int id = order[blockIdx.x];
-  InstDev I = inst[id];
-  if (I.done) return;
-  const int n = I.n;
-  const int stride = nmax + 2 * kBatchGhost;
-  T* R = (T*)smem_raw;
+// The cells one CTA advances: the whole instance, or one half of it when the instance is
+// split over the two CTAs of a cluster.  Local cell c is instance cell lo + c.
+struct Part {
+  int nl;       // own cells 0 .. nl-1
+  int lo;       // instance index of local cell 0
+  int fa, fb;   // Eulerian faces fa .. fb (face f between local cells f-1 and f)
+  int ca, cb;   // Eulerian updates of local cells ca .. cb-1
+  bool gl, gr;  // outflow ghosts left of cell 0 / right of cell nl-1 (the instance's ends)
+};
+
+// CFL step of an instance split over a CTA pair (Sec. 1.1), with the halo exchange.  Each
+// CTA reduces its maxima and publishes them, with its kPairHalo edge cells of the four
+// fields next to the partner, in slot `par` of its shared memory; after the cluster
+// barrier it copies the partner's edge cells into its halo through distributed shared
+// memory, and thread 0 decides from the larger of the two CTAs' maxima (cfl_decide).  Both
+// thread 0s hold the same time and see the same maxima, so both CTAs take the same
+// decisions and meet the same barriers.  The slots alternate with the step's parity: a
+// slot is rewritten two steps later, after the next cluster barrier, which the partner
+// passes only after its reads of this one.  Fields R, M, E, Ei are padded by kPairHalo.
+template <typename T>
+__device__ __forceinline__ bool pair_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
+                                              T* xslot, int par, const Part& P, T* R, T* M,
+                                              T* E, T* Ei, double& dt, T& th) {
+  constexpr int G = kPairHalo;
+  warp_maxima<T>(a, b, sh);
+  __syncthreads();  // orders the step's last stores and the warp maxima
+  T* slot = xslot + par * kPairSlot;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x < 4 * kPairHalo) {  // rank 0 publishes cells nl-6 .. nl-1, rank 1 0 .. 5
+      const int f = threadIdx.x / kPairHalo, k = threadIdx.x % kPairHalo;
+      const T* q = f == 0 ? R : f == 1 ? M : f == 2 ? E : Ei;
+      slot[threadIdx.x] = q[G + (P.gl ? P.nl - kPairHalo : 0) + k];
+    }
+    T A, B;
+    fold_maxima<T>(sh, A, B);
+    if (threadIdx.x == 0) {
+      slot[4 * kPairHalo] = A;
+      slot[4 * kPairHalo + 1] = B;
+    }
+  }
+  cluster_sync();
+  const T* rslot = cooperative_groups::this_cluster().map_shared_rank(slot, cluster_rank() ^ 1u);
+  if (threadIdx.x < 4 * kPairHalo) {  // rank 0's halo is cells nl .. nl+5, rank 1's -6 .. -1
+    const int f = threadIdx.x / kPairHalo, k = threadIdx.x % kPairHalo;
+    T* q = f == 0 ? R : f == 1 ? M : f == 2 ? E : Ei;
+    q[G + (P.gl ? P.nl : -kPairHalo) + k] = rslot[threadIdx.x];
+  }
+  if (threadIdx.x == 0)
+    cfl_decide<T>(fmax(slot[4 * kPairHalo], rslot[4 * kPairHalo]),
+                  fmax(slot[4 * kPairHalo + 1], rslot[4 * kPairHalo + 1]), cfl, I, sh);
+  __syncthreads();
+  dt = sh[64];
+  th = *reinterpret_cast<const T*>(sh + 66);
+  return *reinterpret_cast<const int*>(sh + 68) != 0;
+}
+
+// One CTA's part of an instance advanced for up to max_steps steps (Sec. 1 in 1D).  PAIR:
+// the part is half of an instance and the partner CTA of the cluster holds the other half
+// (halo exchange and common CFL step in pair_cfl_step); else the part is the instance.
+// Local arrays: four fields with G cells of padding on each side (the halo facing the
+// partner, outflow ghosts at the instance's ends), face arrays indexed f + FO.
+template <typename T, int NTHREADS, bool PAIR>
+__device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restrict__ g_m,
+                                             T* __restrict__ g_en, T* __restrict__ g_ei,
+                                             InstDev& I, const Part P, T* smem, int stride,
+                                             int nface, double gamma_d, double cfl,
+                                             int max_steps, double* red, T* xslot) {
+  constexpr int G = PAIR ? kPairHalo : kBatchGhost;
+  constexpr int FO = PAIR ? 3 : 0;
+  const int nl = P.nl;
+  T* R = smem;
   T* M = R + stride;
   T* E = M + stride;
   T* Ei = E + stride;
-  T* FA = Ei + stride;      // face array A (V, then v hat or the rho flux)
-  T* FB = FA + (nmax + 1);  // face array B (P, then fluxes)
-  T* FC = FB + (nmax + 1);  // FP32 only: the rho E and rho eps fluxes
-  T* FD = FC + (nmax + 1);
+  T* FA = Ei + stride;  // face array A (V, then v hat or the rho flux)
+  T* FB = FA + nface;   // face array B (P, then fluxes)
+  T* FC = FB + nface;   // FP32 only: the rho E and rho eps fluxes
+  T* FD = FC + nface;
   const int tid = threadIdx.x;
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
-  // faces per streamed run: one run per thread covers all n + 1 faces; at least 9 (the
+  // faces per streamed run: one run per thread covers the pass's faces; at least 9 (the
   // stream reads 3 extra cells on each side of its run) and odd, so that the runs of the
   // 32 lanes of a warp start on 32 different banks
-  const int run = max(8, (n + 1 + NTHREADS - 1) / NTHREADS) | 1;
+  const int run_e = max(8, (P.fb - P.fa + 1 + NTHREADS - 1) / NTHREADS) | 1;
+  const int run = max(8, (nl + 1 + NTHREADS - 1) / NTHREADS) | 1;
   constexpr int kU = sizeof(T) == 4 ? 4 : 2;  // cells per thread per update pass
   const float rho_vac_up = __double2float_ru(I.rho_vac);  // set by batch_vacuum_kernel
-  // Outflow ghosts of field q from its edge cells, written after a cell pass by the
-  // threads that own those cells (cell c belongs to thread c mod NTHREADS in every cell
-  // pass): they read back their own stores, so no barrier (and no pass) of its own.
-  const int owner_last = (n - 1) % NTHREADS;
-  auto edge_ghosts = [&](T* q) {
-    if (tid == 0) {
-      const T v = q[kBatchGhost];
+  // Outflow ghosts of field q from the edge cells of the instance, written after a cell
+  // pass that starts at cell `base` by the threads that own those cells in it (cell c
+  // belongs to thread (c - base) mod NTHREADS): they read back their own stores, so no
+  // barrier (and no pass) of its own.
+  auto outer_ghosts = [&](T* q, int base) {
+    if (P.gl && tid == (0 - base) % NTHREADS) {
+      const T v = q[G];
 #pragma unroll
-      for (int k = 0; k < kBatchGhost; k++) q[k] = v;
+      for (int k = 1; k <= kBatchGhost; k++) q[G - k] = v;
     }
-    if (tid == owner_last) {
-      const T v = q[n + kBatchGhost - 1];
+    if (P.gr && tid == (nl - 1 - base) % NTHREADS) {
+      const T v = q[G + nl - 1];
 #pragma unroll
-      for (int k = 0; k < kBatchGhost; k++) q[n + kBatchGhost + k] = v;
+      for (int k = 0; k < kBatchGhost; k++) q[G + nl + k] = v;
     }
   };
   // CFL maxima (Sec. 1.1) over the cells a thread owns, taken as each cell's final value
@@ -329,57 +415,72 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
     vm = valid ? fmax(vm, v) : vm;
     cm = valid ? fmax(cm, cs) : cm;
   };
-  for (int c = tid; c < n; c += blockDim.x) {
-    const int g = c + kBatchGhost;
-    const T r = g_rho[I.off + c], m = g_m[I.off + c], en = g_en[I.off + c], ei = g_ei[I.off + c];
+  const long long off = I.off + P.lo;
+  for (int c = tid; c < nl; c += NTHREADS) {
+    const int g = c + G;
+    const T r = g_rho[off + c], m = g_m[off + c], en = g_en[off + c], ei = g_ei[off + c];
     R[g] = r;
     M[g] = m;
     E[g] = en;
     Ei[g] = ei;
     cfl_cell(r, m, ei, true);
   }
-  edge_ghosts(R);
-  edge_ghosts(M);
-  edge_ghosts(E);
-  edge_ghosts(Ei);
-  // Upwind Lagrangian fluxes of one field at the faces of every thread's run (Sec. 1.3)
+  outer_ghosts(R, 0);
+  outer_ghosts(M, 0);
+  outer_ghosts(E, 0);
+  outer_ghosts(Ei, 0);
+  if constexpr (PAIR) {  // the initial halo: the partner's first cells, from the state
+    const int h0 = P.gl ? nl : -kPairHalo;  // local index of the halo's first cell
+    if (tid < kPairHalo) {
+      const long long gi = off + h0 + tid;
+      R[G + h0 + tid] = g_rho[gi];
+      M[G + h0 + tid] = g_m[gi];
+      E[G + h0 + tid] = g_en[gi];
+      Ei[G + h0 + tid] = g_ei[gi];
+    }
+  }
+  // Upwind Lagrangian fluxes of one field at the own faces 0 .. nl (Sec. 1.3)
   auto lagrangian_fluxes = [&](const T* q, double dt, T th) {
-    auto qq = [&](int c) { return q[c + kBatchGhost]; };
-    for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
-      const int f1 = min(f0 + run - 1, n);
+    auto qq = [&](int c) { return q[c + G]; };
+    for (int f0 = tid * run; f0 <= nl; f0 += NTHREADS * run) {
+      const int f1 = min(f0 + run - 1, nl);
       stream_faces<T>(qq, f0, f1, [&](int f, const Parab<T>& PL, const Parab<T>& PR) {
-        const T vh = FA[f];
+        const T vh = FA[f + FO];
         const T y = Prec<T>::courant(tabs(vh), dt, I.h, th);
-        FB[f] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y)
-                           : vh * avg_left(PR.L, PR.D, PR.S, y);
+        FB[f + FO] = vh >= T(0) ? vh * avg_right(PL.R, PL.D, PL.S, y)
+                                : vh * avg_left(PR.L, PR.D, PR.S, y);
       });
     }
   };
-  // Barriers per step: two in the CFL reduction (the first also orders every field and
-  // ghost write of the previous step), Eulerian faces, Eulerian update, then in FP32 one
+  // Barriers per step: the CFL reduction (two; in a pair one CTA barrier, the cluster
+  // barrier and one more CTA barrier), Eulerian faces, Eulerian update, then in FP32 one
   // after the Lagrangian flux pass; in FP64 one after v hat and two per Lagrangian field
   // but the last.  The last update pass also applies the energy correction, writes the
   // ghosts and takes the next step's CFL maxima.
   for (int s = 0; s < max_steps; s++) {
     double dt;
     T th;
-    if (!block_cfl_step<T>(vm, cm, cfl, I, red, dt, th)) break;
-    // Eulerian stage: faces f = 0..n (between cells f-1 and f, padded cells f+2 and f+3);
-    // each thread streams one run of `run` consecutive faces
+    bool go;
+    if constexpr (PAIR)
+      go = pair_cfl_step<T>(vm, cm, cfl, I, red, xslot, s & 1, P, R, M, E, Ei, dt, th);
+    else
+      go = block_cfl_step<T>(vm, cm, cfl, I, red, dt, th);
+    if (!go) break;
+    // Eulerian stage: faces fa .. fb; each thread streams one run of consecutive faces
     {
-      auto vq = [&](int k) { return vel_of(M[k + kBatchGhost], R[k + kBatchGhost]); };
-      auto pq = [&](int k) { return gm1 * Ei[k + kBatchGhost]; };
-      for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
-        const int f1 = min(f0 + run - 1, n);
+      auto vq = [&](int k) { return vel_of(M[k + G], R[k + G]); };
+      auto pq = [&](int k) { return gm1 * Ei[k + G]; };
+      for (int f0 = P.fa + tid * run_e; f0 <= P.fb; f0 += NTHREADS * run_e) {
+        const int f1 = min(f0 + run_e - 1, P.fb);
         // rho and sqrt(rho) of the face's left cell, carried from the previous face
-        T r_l = R[f0 + 2], s_l = T(0);
+        T r_l = R[f0 - 1 + G], s_l = T(0);
         if constexpr (sizeof(T) == 4) s_l = sqrt_approx(r_l);
         stream_faces2<T>(vq, pq, f0, f1,
                          [&](int f, T, T, const Parab<T>& vL, const Parab<T>& vR, T pl, T pr,
                              const Parab<T>& pL, const Parab<T>& pR) {
-          const T rl = r_l, rr = R[f + 3];
+          const T rl = r_l, rr = R[f + G];
           r_l = rr;
-          T V, P;
+          T V, Pf;
           if constexpr (sizeof(T) == 4) {
             float lam, Z, hrz;
             const float sl = s_l, sr = sqrt_approx(rr);
@@ -389,39 +490,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
             const float vls = avg_right(vL.R, vL.D, vL.S, y), vrs = avg_left(vR.L, vR.D, vR.S, y);
             const float pls = avg_right(pL.R, pL.D, pL.S, y), prs = avg_left(pR.L, pR.D, pR.S, y);
             V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
-            P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
+            Pf = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
           } else {
             T lam, Z;
             face_constants(rl, rr, pl, pr, gamma, lam, Z);
             const T y = Prec<T>::courant(lam, dt, I.h, th);
             riemann_vp(avg_right(vL.R, vL.D, vL.S, y), avg_left(vR.L, vR.D, vR.S, y),
-                       avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, P);
+                       avg_right(pL.R, pL.D, pL.S, y), avg_left(pR.L, pR.D, pR.S, y), Z, V, Pf);
           }
-          FA[f] = V;
-          FB[f] = P;
+          FA[f + FO] = V;
+          FB[f + FO] = Pf;
         });
       }
     }
     __syncthreads();
     // cells c0 + u NTHREADS, u < kU, per pass: every load of the pass ahead of its stores
     // (the compiler cannot move a load past a store into the same shared array)
-    for (int c0 = tid; c0 < n; c0 += kU * NTHREADS) {
+    for (int c0 = P.ca + tid; c0 < P.cb; c0 += kU * NTHREADS) {
       T Vm[kU], Vp[kU], Pm[kU], Pp[kU], m0[kU], e0[kU], ei0[kU];
 #pragma unroll
       for (int u = 0; u < kU; u++) {
-        const int c = min(c0 + u * NTHREADS, n - 1), g = c + kBatchGhost;
-        Vm[u] = FA[c];
-        Vp[u] = FA[c + 1];
-        Pm[u] = FB[c];
-        Pp[u] = FB[c + 1];
+        const int c = min(c0 + u * NTHREADS, P.cb - 1), g = c + G;
+        Vm[u] = FA[c + FO];
+        Vp[u] = FA[c + 1 + FO];
+        Pm[u] = FB[c + FO];
+        Pp[u] = FB[c + 1 + FO];
         m0[u] = M[g];
         e0[u] = E[g];
         ei0[u] = Ei[g];
       }
 #pragma unroll
       for (int u = 0; u < kU; u++) {
-        const int c = c0 + u * NTHREADS, g = c + kBatchGhost;
-        if (c < n) {
+        const int c = c0 + u * NTHREADS, g = c + G;
+        if (c < P.cb) {
           const T m1 = m0[u] - th * (Pp[u] - Pm[u]);
           const T e1 = e0[u] - th * (Pp[u] * Vp[u] - Pm[u] * Vm[u]);
           const T ei1 = ei0[u] - gm1 * ei0[u] * (th * (Vp[u] - Vm[u]));
@@ -431,22 +532,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         }
       }
     }
-    edge_ghosts(M);
-    edge_ghosts(E);
-    edge_ghosts(Ei);
+    outer_ghosts(M, P.ca);
+    outer_ghosts(E, P.ca);
+    outer_ghosts(Ei, P.ca);
     __syncthreads();
     if constexpr (sizeof(T) == 4) {
       // Lagrangian stage in one pass over each run of faces: v hat (eq. veltemplate with
       // the Roe weights, Sec. 1.3) from the streamed rho and m, each cell's template and
       // sqrt(rho) formed once and carried to the next face, then the upwind fluxes of all
       // four fields
-      auto q4 = [&](int j, int k) {
-        return (j == 0 ? R : j == 1 ? M : j == 2 ? E : Ei)[k + kBatchGhost];
-      };
-      for (int f0 = tid * run; f0 <= n; f0 += NTHREADS * run) {
-        const int f1 = min(f0 + run - 1, n);
-        const float r0 = R[f0 + 2];  // cell f0-1
-        float vt_l = template_1d(vel_of(M[f0 + 2], r0)), s_l = sqrt_approx(r0);
+      auto q4 = [&](int j, int k) { return (j == 0 ? R : j == 1 ? M : j == 2 ? E : Ei)[k + G]; };
+      for (int f0 = tid * run; f0 <= nl; f0 += NTHREADS * run) {
+        const int f1 = min(f0 + run - 1, nl);
+        const float r0 = R[f0 - 1 + G];  // cell f0-1
+        float vt_l = template_1d(vel_of(M[f0 - 1 + G], r0)), s_l = sqrt_approx(r0);
         stream_faces_n<float, 4>(q4, f0, f1,
                                  [&](int f, const float*, const float* c, const Parab<float>* PL,
                                      const Parab<float>* PR) {
@@ -460,10 +559,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
           for (int j = 0; j < 4; j++)
             F[j] = vh >= 0.0f ? vh * avg_right(PL[j].R, PL[j].D, PL[j].S, y)
                               : vh * avg_left(PR[j].L, PR[j].D, PR[j].S, y);
-          FA[f] = F[0];
-          FB[f] = F[1];
-          FC[f] = F[2];
-          FD[f] = F[3];
+          FA[f + FO] = F[0];
+          FB[f + FO] = F[1];
+          FC[f + FO] = F[2];
+          FD[f + FO] = F[3];
         });
       }
       __syncthreads();
@@ -471,15 +570,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       // step's CFL maxima, cell by cell
       vm = T(0);
       cm = T(0);
-      for (int c0 = tid; c0 < n; c0 += kU * NTHREADS) {
+      for (int c0 = tid; c0 < nl; c0 += kU * NTHREADS) {
         float q[kU][4];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
-          const int c = min(c0 + u * NTHREADS, n - 1), g = c + kBatchGhost;
-          q[u][0] = R[g] - th * (FA[c + 1] - FA[c]);
-          q[u][1] = M[g] - th * (FB[c + 1] - FB[c]);
-          q[u][2] = E[g] - th * (FC[c + 1] - FC[c]);
-          q[u][3] = Ei[g] - th * (FD[c + 1] - FD[c]);
+          const int c = min(c0 + u * NTHREADS, nl - 1), g = c + G;
+          q[u][0] = R[g] - th * (FA[c + 1 + FO] - FA[c + FO]);
+          q[u][1] = M[g] - th * (FB[c + 1 + FO] - FB[c + FO]);
+          q[u][2] = E[g] - th * (FC[c + 1 + FO] - FC[c + FO]);
+          q[u][3] = Ei[g] - th * (FD[c + 1 + FO] - FD[c + FO]);
         }
         // Sec. 1.4: the dense branch for all kU cells without control flow (so that
         // their chains interleave), then the rare vacuum cells
@@ -508,8 +607,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         }
 #pragma unroll
         for (int u = 0; u < kU; u++) {
-          const int c = c0 + u * NTHREADS, g = c + kBatchGhost;
-          if (c < n) {
+          const int c = c0 + u * NTHREADS, g = c + G;
+          if (c < nl) {
             R[g] = q[u][0];
             M[g] = q[u][1];
             E[g] = q[u][2];
@@ -519,19 +618,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         // next step's CFL maxima over the valid cells (a clamped duplicate may have read
         // a cell its owner has already updated)
 #pragma unroll
-        for (int u = 0; u < kU; u++) cfl_cell(q[u][0], q[u][1], q[u][3], c0 + u * NTHREADS < n);
+        for (int u = 0; u < kU; u++) cfl_cell(q[u][0], q[u][1], q[u][3], c0 + u * NTHREADS < nl);
       }
-      edge_ghosts(R);
-      edge_ghosts(M);
-      edge_ghosts(E);
-      edge_ghosts(Ei);
     } else {
       // FP64 Lagrangian stage: v hat at faces, then each field's flux and update in turn
-      for (int f = tid; f <= n; f += blockDim.x) {
-        const T rl = R[f + 2], rr = R[f + 3];
-        const T vtl = template_1d(vel_of(M[f + 2], rl)), vtr = template_1d(vel_of(M[f + 3], rr));
+      for (int f = tid; f <= nl; f += NTHREADS) {
+        const T rl = R[f - 1 + G], rr = R[f + G];
+        const T vtl = template_1d(vel_of(M[f - 1 + G], rl)), vtr = template_1d(vel_of(M[f + G], rr));
         const T sl = sqrt(rl), sr = sqrt(rr);
-        FA[f] = (vtr * sr + vtl * sl) / (sr + sl);
+        FA[f + FO] = (vtr * sr + vtl * sl) / (sr + sl);
       }
       __syncthreads();
       T* fields[3] = {R, M, E};
@@ -540,8 +635,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
         T* q = fields[k];
         lagrangian_fluxes(q, dt, th);
         __syncthreads();
-        for (int c = tid; c < n; c += blockDim.x)
-          q[c + kBatchGhost] = q[c + kBatchGhost] - th * (FB[c + 1] - FB[c]);
+        for (int c = tid; c < nl; c += NTHREADS)
+          q[c + G] = q[c + G] - th * (FB[c + 1 + FO] - FB[c + FO]);
         __syncthreads();
       }
       lagrangian_fluxes(Ei, dt, th);
@@ -549,30 +644,106 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
       // rho eps update, then the Sec. 1.4 energy consistency, on the same cells
       vm = T(0);
       cm = T(0);
-      for (int c = tid; c < n; c += blockDim.x) {
-        const int g = c + kBatchGhost;
+      for (int c = tid; c < nl; c += NTHREADS) {
+        const int g = c + G;
         const T r = R[g], en = E[g];
-        T u[6] = {r, M[g], T(0), T(0), en, Ei[g] - th * (FB[c + 1] - FB[c])};
+        T u[6] = {r, M[g], T(0), T(0), en, Ei[g] - th * (FB[c + 1 + FO] - FB[c + FO])};
         correct_energy<T>(u, I.rho_vac);
         M[g] = u[1];
         Ei[g] = u[5];
         cfl_cell(r, u[1], u[5], true);
       }
-      edge_ghosts(R);
-      edge_ghosts(M);
-      edge_ghosts(E);
-      edge_ghosts(Ei);
     }
+    outer_ghosts(R, 0);
+    outer_ghosts(M, 0);
+    outer_ghosts(E, 0);
+    outer_ghosts(Ei, 0);
   }
-  for (int c = tid; c < n; c += blockDim.x) {
-    g_rho[I.off + c] = R[c + kBatchGhost];
-    g_m[I.off + c] = M[c + kBatchGhost];
-    g_en[I.off + c] = E[c + kBatchGhost];
-    g_ei[I.off + c] = Ei[c + kBatchGhost];
+  if constexpr (PAIR) cluster_sync();  // the partner may still read this CTA's slot
+  for (int c = tid; c < nl; c += NTHREADS) {
+    g_rho[off + c] = R[c + G];
+    g_m[off + c] = M[c + G];
+    g_en[off + c] = E[c + G];
+    g_ei[off + c] = Ei[c + G];
   }
-  if (tid == 0) {  // thread 0's copy holds the instance's time
+}
+
+template <typename T, int NTHREADS>
+__global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rho,
+                                                              T* __restrict__ g_m,
+                                                              T* __restrict__ g_en,
+                                                              T* __restrict__ g_ei,
+                                                              InstDev* __restrict__ inst,
+                                                              const int* __restrict__ order,
+                                                              double gamma_d, double cfl,
+                                                              int max_steps, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[80];
+  const int id = order[blockIdx.x];
+  InstDev I = inst[id];
+  if (I.done) return;
+  const Part P{I.n, 0, 0, I.n, 0, I.n, true, true};
+  advance_part<T, NTHREADS, false>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
+                                   nmax + 2 * kBatchGhost, nmax + 1, gamma_d, cfl, max_steps,
+                                   red, nullptr);
+  if (threadIdx.x == 0) {  // thread 0's copy holds the instance's time
     if (I.t >= I.t_end) I.done = 1;
     inst[id] = I;
+  }
+}
+
+// Work item of one cluster of two CTAs (the launch used when some instances are split):
+// y == kItemSplit: instance x split over the pair (rank 0 owns cells [0, n/2), rank 1 the
+// rest, each with a halo of kPairHalo cells on the side facing its partner); otherwise
+// CTA 0 advances instance x and CTA 1 instance y (-1: none), each alone.  Items are
+// ordered largest first, so the longest runs take SMs first.
+constexpr int kItemSplit = -2;
+
+// In a split instance each CTA forms the Eulerian faces and updates of its cells and of
+// the 3 halo cells next to them (its Lagrangian stream reads 3 cells past its last face),
+// then the Lagrangian stage of its own faces and cells; the face between the halves is
+// formed by both from the same values.  The halo and the CFL maxima are exchanged once
+// per step (pair_cfl_step).  Both CTAs of a split item take the same branch and the same
+// decisions, so they meet the same cluster barriers; the CTAs of a two-instance item
+// never wait on each other.  A split instance needs n >= 2 kPairHalo.
+template <typename T, int NTHREADS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    batch_cluster_kernel(T* __restrict__ g_rho, T* __restrict__ g_m, T* __restrict__ g_en,
+                         T* __restrict__ g_ei, InstDev* __restrict__ inst,
+                         const int2* __restrict__ items, double gamma_d, double cfl,
+                         int max_steps, int nlmax, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[80];
+  __shared__ T xslot[2][kPairSlot];
+  const int rank = (int)cluster_rank();
+  const int2 item = items[blockIdx.x >> 1];
+  if (item.y == kItemSplit) {
+    const int id = item.x;
+    InstDev I = inst[id];
+    if (I.done) return;  // both CTAs of the pair read the same flag
+    const int n = I.n, n0 = n / 2;
+    const Part P = rank == 0 ? Part{n0, 0, 0, n0 + 3, 0, n0 + 3, true, false}
+                             : Part{n - n0, n0, -3, n - n0, -3, n - n0, false, true};
+    advance_part<T, NTHREADS, true>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
+                                    nlmax + 2 * kPairHalo, nlmax + 8, gamma_d, cfl, max_steps,
+                                    red, &xslot[0][0]);
+    if (rank == 0 && threadIdx.x == 0) {  // both CTAs hold the same time; rank 0 stores it
+      if (I.t >= I.t_end) I.done = 1;
+      inst[id] = I;
+    }
+  } else {
+    const int id = rank == 0 ? item.x : item.y;
+    if (id < 0) return;
+    InstDev I = inst[id];
+    if (I.done) return;
+    const Part P{I.n, 0, 0, I.n, 0, I.n, true, true};
+    advance_part<T, NTHREADS, false>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
+                                     nmax + 2 * kBatchGhost, nmax + 1, gamma_d, cfl, max_steps,
+                                     red, nullptr);
+    if (threadIdx.x == 0) {
+      if (I.t >= I.t_end) I.done = 1;
+      inst[id] = I;
+    }
   }
 }
 

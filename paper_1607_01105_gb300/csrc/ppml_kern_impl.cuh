@@ -104,17 +104,58 @@ int launch_batch_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei, 
                                                        max_steps, nmax);
   return ppml_check_launch("batch_kernel");
 }
+
+template <int NT>
+int launch_cluster_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei, InstDev* inst,
+                      const int2* items, double gamma, double cfl, int max_steps, int nlmax,
+                      int nmax, int nitems, size_t smem, cudaStream_t st) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_cluster_kernel<PPML_REAL, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+      return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    configured = smem;
+  }
+  batch_cluster_kernel<PPML_REAL, NT><<<2 * nitems, NT, smem, st>>>(
+      rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax, nmax);
+  return ppml_check_launch("batch_cluster_kernel");
+}
 }  // namespace
+
+template <>
+int launch_batch_vacuum<PPML_REAL>(const PPML_REAL* rho, InstDev* inst, int ninst,
+                                   cudaStream_t st) {
+  // vacuum thresholds of instances not yet started (no-op for the others)
+  batch_vacuum_kernel<PPML_REAL><<<ninst, 256, 0, st>>>(rho, inst);
+  return ppml_check_launch("batch_vacuum_kernel");
+}
+
+template <>
+int launch_batch_cluster<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                                    InstDev* inst, const int2* items, double gamma, double cfl,
+                                    int max_steps, int nlmax, int nmax, int nitems, size_t smem,
+                                    int threads, cudaStream_t st) {
+  switch (threads) {
+    case 256:
+      return launch_cluster_nt<256>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+                                    nmax, nitems, smem, st);
+    case 512:
+      return launch_cluster_nt<512>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+                                    nmax, nitems, smem, st);
+    case 1024:
+      return launch_cluster_nt<1024>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+                                     nmax, nitems, smem, st);
+    default:
+      return ppml_fail(PPML_E_INVAL, "batch CTA size %d is not 256, 512 or 1024", threads);
+  }
+}
 
 template <>
 int launch_batch<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
                             InstDev* inst, const int* order, double gamma, double cfl,
                             int max_steps, int nmax, int ninst, size_t smem, int threads,
                             cudaStream_t st) {
-  // vacuum thresholds of instances not yet started (no-op for the others)
-  batch_vacuum_kernel<PPML_REAL><<<ninst, 256, 0, st>>>(rho, inst);
-  int rc = ppml_check_launch("batch_vacuum_kernel");
-  if (rc) return rc;
   switch (threads) {
     case 256:
       return launch_batch_nt<256>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax, ninst,

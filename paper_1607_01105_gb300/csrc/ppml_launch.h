@@ -21,10 +21,20 @@ int launch_diag(const MarchArgs<T>& A, int nblk, cudaStream_t st);
 template <typename T>
 int launch_poisson_symbol(void* spec, const double* tx, const double* ty, const double* tz, int mx,
                           int ny, int nz, double coef, cudaStream_t st);
+// Batched 1D problems: the vacuum thresholds of all ninst instances (instance = CTA index),
+// then one CTA per instance of order[0 .. ninst), or one cluster of two CTAs per work item
+// of items[0 .. nitems) (nlmax: the largest half of a split instance, nmax: the largest
+// instance taken by one CTA).
+template <typename T>
+int launch_batch_vacuum(const T* rho, InstDev* inst, int ninst, cudaStream_t st);
 template <typename T>
 int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
                  double cfl, int max_steps, int nmax, int ninst, size_t smem, int threads,
                  cudaStream_t st);
+template <typename T>
+int launch_batch_cluster(T* rho, T* m, T* en, T* ei, InstDev* inst, const int2* items,
+                         double gamma, double cfl, int max_steps, int nlmax, int nmax,
+                         int nitems, size_t smem, int threads, cudaStream_t st);
 
 // Deterministic reduction of per-CTA partials into the step scalars (ppml_grid.cu).
 int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
@@ -45,9 +55,16 @@ int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, doubl
                                const double* tz, int mx, int ny, int nz, double coef,          \
                                cudaStream_t st);                                               \
   template <>                                                                                \
+  int launch_batch_vacuum<R>(const R* rho, InstDev* inst, int ninst, cudaStream_t st);        \
+  template <>                                                                                \
   int launch_batch<R>(R * rho, R * m, R * en, R * ei, InstDev * inst, const int* order,       \
                       double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem, \
-                      int threads, cudaStream_t st);
+                      int threads, cudaStream_t st);                                           \
+  template <>                                                                                \
+  int launch_batch_cluster<R>(R * rho, R * m, R * en, R * ei, InstDev * inst,                 \
+                              const int2* items, double gamma, double cfl, int max_steps,      \
+                              int nlmax, int nmax, int nitems, size_t smem, int threads,       \
+                              cudaStream_t st);
 PPML_DECLARE_LAUNCHERS(float)
 PPML_DECLARE_LAUNCHERS(double)
 #undef PPML_DECLARE_LAUNCHERS

@@ -29,7 +29,8 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_batch_step", "ppml_batch_status", "ppml_batch_free", "ppml_last_error",
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
-            "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak")
+            "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak",
+            "ppml_batch_set_split")
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -76,6 +77,7 @@ _lib.ppml_poisson_isolated.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_
 _lib.ppml_batch_tune.argtypes = [_vp, ctypes.c_void_p * 4, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_batch_set_threads.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_batch_set_split.argtypes = [_vp, ctypes.c_int]
 _lib.ppml_fourier_amplitudes.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
@@ -309,6 +311,10 @@ class Batch:
         _check(_lib.ppml_batch_tune(self._h, ptrs, int(trial_steps), ctypes.byref(chosen), ms,
                                     _stream(stream)))
         return chosen.value, dict(zip((256, 512, 1024), list(ms)))
+
+    def set_split(self, min_cells):
+        """Instances of at least min_cells cells take a CTA pair (0: none)."""
+        _check(_lib.ppml_batch_set_split(self._h, int(min_cells)))
 
     def set_threads(self, threads):
         _check(_lib.ppml_batch_set_threads(self._h, int(threads)))

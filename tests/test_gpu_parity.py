@@ -506,6 +506,65 @@ def test_config4_batch_cta_sizes_fp64_bitwise(threads):
             assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
 
 
+@pytest.mark.parametrize("split", [64, 600, 0])
+def test_config4_batch_pairs_fp64_bitwise(split):
+    """Instances split over the two CTAs of a cluster (halves that exchange a 6-cell halo
+    and their CFL maxima through distributed shared memory once per step) give the
+    oracle's result bit for bit (FP64): every instance paired (64), paired ones beside
+    one-CTA ones (600), none paired (0)."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=12, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    bt.set_split(split)
+    bt.set_threads(256)
+    st = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    for _ in range(100):
+        if bt.step(st, 300, sync=True) == b.ncells.size:
+            break
+    got = [x.cpu().numpy() for x in st]
+    t, steps = bt.status()
+    for i in range(b.ncells.size):
+        ref, steps_o = _batch_oracle_run(b, i)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        assert steps[i] == steps_o, (i, steps[i], steps_o)
+        for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+            assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
+
+
+def test_config4_batch_pairs_fp32_match_one_cta():
+    """FP32: the paired and the one-CTA launches take the same steps and agree in rho and
+    rho eps to the config-4 bar, relative L1 within max(1e-4, 2 S_i), S_i the change of the
+    FP64 oracle when its state is stored in float32 between steps: the two kernels are
+    compiled separately and may contract different products into FMAs, and such last-bit
+    differences grow over the runs' thousands of steps like any FP32 rounding (2e-6 to
+    3e-5 measured).  Invalid split sizes are rejected and keep the previous split."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=12, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
+    out = {}
+    for split in (0, 64, 600):
+        bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F32)
+        bt.set_split(split)
+        st = [torch.as_tensor(a).to("cuda", torch.float32) for a in b.u]
+        assert bt.step(st, 1 << 30, sync=True) == b.ncells.size
+        out[split] = ([x.double().cpu().numpy() for x in st], bt.status()[1])
+        if split == 64:
+            for bad in (10, -5):
+                with pytest.raises(ppml.PPMLError):
+                    bt.set_split(bad)
+        bt.close()
+    ref, ref_steps = out[0]
+    for split in (64, 600):
+        got, steps = out[split]
+        assert list(steps) == list(ref_steps), split
+        for i in range(b.ncells.size):
+            sl = slice(b.offsets[i], b.offsets[i + 1])
+            e = max(rel_l1(got[k][sl], ref[k][sl]) for k in (0, 3))
+            tol = 1e-4
+            if e > tol:
+                tol = max(tol, 2.0 * _fp32_storage_sensitivity(b, i, _batch_oracle(b, i)[0]))
+            assert e <= tol, (split, i, e, tol)
+
+
 def test_config4_batch_tune_leaves_state_and_progress():
     """The autotuner times the three CTA sizes on scratch copies: the caller's state and
     the instances' times are unchanged, the chosen size is one of the three and is the
