@@ -273,7 +273,7 @@ int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps, int* t
  * use two SMs.  The launch is then one grid of two-CTA clusters, each taking a split
  * instance or two whole instances of neighbouring sizes (one per CTA), largest first.
  * min_cells = 0: no split (one CTA per instance).  ppml_batch_init selects
- * max(256, ceil(7 largest / 8)).  Results do not depend on the split (the same operations
+ * max(1024, ceil(7 largest / 8)).  Results do not depend on the split (the same operations
  * per cell, in the same order); the work plan is rebuilt (host to device copy).
  * PPML_E_INVAL for 0 < min_cells < 64 or if an instance would not fit (the previous
  * split is kept). */

@@ -169,9 +169,10 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
   b->cfl = cfl;
   b->ncells.assign(ncells, ncells + n_inst);
   b->threads = 512;
-  // default split: the instances within 1/8 of the largest size (and of at least 256
-  // cells) take a CTA pair, so the longest runs are not left to one SM each
-  b->split_min = std::max(256, (7 * nmax + 7) / 8);
+  // default split: the instances within 1/8 of the largest size take a CTA pair, so the
+  // longest runs are not left to one SM each; below 1024 cells the per-step exchange
+  // costs more than the halved work saves
+  b->split_min = std::max(1024, (7 * nmax + 7) / 8);
   int rc = PPML_OK;
   if (cudaMalloc(&b->inst, sizeof(InstDev) * n_inst) != cudaSuccess ||
       cudaMalloc(&b->order, sizeof(int) * n_inst) != cudaSuccess ||
