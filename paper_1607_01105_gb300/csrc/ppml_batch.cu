@@ -1,5 +1,6 @@
-// Host side of the batched independent 1D problems (ppml_batch_*): instance metadata,
-// largest-work-first launch order and the persistent launch (kernel in ppml_batch.cuh).
+// Host side of the batched independent 1D problems (ppml_batch_*): instance metadata, the
+// work plan (which instances are split over a two-CTA cluster, largest-first order) and
+// the persistent launch (kernels in ppml_batch.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>

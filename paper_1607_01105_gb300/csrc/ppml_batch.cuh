@@ -1,13 +1,14 @@
 // Batched independent 1D problems (many shock tubes of uneven lengths) advanced by one
-// persistent launch: each CTA owns one instance, keeps its four fields (rho, m, rho E,
-// rho eps) resident in shared memory for all of its steps, takes its own CFL step from a
-// CTA-local reduction (Sec. 1.1) and stops at its own end time.  The scheme per step is
-// the 1D case of Sec. 1: Eulerian face solve, upwind Lagrangian fluxes, energy
-// correction of Sec. 1.4.  In 1D the 9-point template (eq. veltemplate) runs on the cell
-// itself (its transverse neighbours are the cell), evaluated term by term.  Outflow
-// boundaries on both ends.  CTAs never wait on one another.  The CTA size (threads per
-// instance) is a template parameter; the host picks it by timing the candidates on the
-// actual batch (ppml_batch_tune).
+// persistent launch: each instance keeps its four fields (rho, m, rho E, rho eps) resident
+// in shared memory for all of its steps, takes its own CFL step (Sec. 1.1) and stops at its
+// own end time.  An instance is owned by one CTA, or -- the longest ones -- split over the
+// two CTAs of a cluster, which exchange a halo and their CFL maxima once per step; no
+// other CTAs wait on one another.  The scheme per step is the 1D case of Sec. 1: Eulerian
+// face solve, upwind Lagrangian fluxes, energy correction of Sec. 1.4.  In 1D the 9-point
+// template (eq. veltemplate) runs on the cell itself (its transverse neighbours are the
+// cell), evaluated term by term.  Outflow boundaries on both ends.  The CTA size is a
+// template parameter; the host picks it by timing the candidates on the actual batch
+// (ppml_batch_tune).
 #pragma once
 #include <cooperative_groups.h>
 
