@@ -293,7 +293,7 @@ __device__ __forceinline__ void stage_box_fast(T* box, const T* __restrict__ src
 // 1: acc += div; 2: dst[c gs] = core - (acc + div) for c < nvalid (acc only if have_acc).
 // The pipeline forms, when position p arrives, the slope at p-1, the face at p-3/2, the
 // parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
-// peeled and the steady state is a rolled loop.
+// peeled and the steady state is a loop unrolled by two.
 template <typename T, int MODE, bool FLAT>
 __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, const T* vh, T th,
                                          double tau, double h, T* acc, bool have_acc,
