@@ -279,6 +279,17 @@ int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps, int* t
  * split is kept). */
 int ppml_batch_set_split(ppml_batch* b, int min_cells);
 
+/* The work plan of a batch of n_inst instances of ncells[i] cells for a split threshold
+ * split_min (0, or >= 64), as ppml_batch_init / ppml_batch_set_split build it; host only,
+ * no device call.  If some instance has at least split_min cells, *n_items work items of
+ * two ints are written to items (room for 2 n_inst ints), largest first by the size of the
+ * item's largest instance: (a, -2) is instance a split over a CTA pair, (a, b) runs
+ * instances a and b on the two CTAs of a cluster (b = -1: none), whole instances paired in
+ * order of size.  Otherwise *n_items = 0 and, if order is non-NULL, order (n_inst ints)
+ * receives the instances largest first (one CTA each).  Ties keep the instances' order. */
+int ppml_batch_plan(int n_inst, const int* ncells, int split_min, int* items, int* n_items,
+                    int* order);
+
 /* Per-instance time reached and steps taken (host arrays of n_inst).  Synchronizes. */
 int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream);
 

@@ -41,24 +41,28 @@ size_t batch_smem(int cells, int pad, int nface, int faces, size_t elt) {
   return (4 * (size_t)(cells + 2 * pad) + (size_t)nface * faces) * elt;
 }
 
-// Work plan for b->split_min: with no instance split, one CTA per instance (largest
-// first); else one cluster of two CTAs per work item -- a split instance, or two one-CTA
-// instances of neighbouring sizes -- ordered largest first by the size of the item's
-// largest instance.  Sizes the launch's shared memory.
+// Work plan for b->split_min (ppml_batch_plan): with no instance split, one CTA per
+// instance (largest first); else one cluster of two CTAs per work item, ordered largest
+// first.  Sizes the launch's shared memory and copies the plan to the device.
 int plan_batch(ppml_batch* b) {
   const size_t elt = b->dtype == PPML_F64 ? 8 : 4;
   const int nface = b->dtype == PPML_F64 ? kBatchFaceArrays<double> : kBatchFaceArrays<float>;
-  std::vector<int> split, rest;
-  for (int i = 0; i < b->n_inst; i++)
-    (b->split_min > 0 && b->ncells[i] >= b->split_min ? split : rest).push_back(i);
-  auto by_size = [&](int x, int y) { return b->ncells[x] > b->ncells[y]; };
-  std::stable_sort(split.begin(), split.end(), by_size);
-  std::stable_sort(rest.begin(), rest.end(), by_size);
-  int nlmax = 0, nmax = 0;
-  for (int i : split) nlmax = std::max(nlmax, b->ncells[i] - b->ncells[i] / 2);
-  for (int i : rest) nmax = std::max(nmax, b->ncells[i]);
-  const size_t smem_split = split.empty() ? 0 : batch_smem(nlmax, kPairHalo, nface, nlmax + 8, elt);
-  const size_t smem_one = rest.empty() ? 0 : batch_smem(nmax, kBatchGhost, nface, nmax + 1, elt);
+  std::vector<int> items(2 * (size_t)b->n_inst), order(b->n_inst);
+  int n_items = 0;
+  int rc = ppml_batch_plan(b->n_inst, b->ncells.data(), b->split_min, items.data(), &n_items,
+                           order.data());
+  if (rc) return rc;
+  int nlmax = 0, nmax = 0, n_split = 0;
+  for (int i = 0; i < b->n_inst; i++) {
+    if (n_items > 0 && b->split_min > 0 && b->ncells[i] >= b->split_min) {
+      nlmax = std::max(nlmax, b->ncells[i] - b->ncells[i] / 2);
+      n_split++;
+    } else {
+      nmax = std::max(nmax, b->ncells[i]);
+    }
+  }
+  const size_t smem_split = n_split ? batch_smem(nlmax, kPairHalo, nface, nlmax + 8, elt) : 0;
+  const size_t smem_one = nmax ? batch_smem(nmax, kBatchGhost, nface, nmax + 1, elt) : 0;
   const size_t smem = std::max(smem_split, smem_one);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
@@ -68,26 +72,16 @@ int plan_batch(ppml_batch* b) {
                      "largest instance needs %zu bytes of shared memory (> %d): %d cells on one "
                      "CTA, %d cells per CTA of a split one",
                      smem, maxsm, nmax, nlmax);
-  std::vector<int2> items;
-  if (!split.empty()) {
-    std::vector<std::pair<int, int2>> keyed;  // (largest size, item)
-    for (int i : split) keyed.push_back({b->ncells[i], make_int2(i, kItemSplit)});
-    for (size_t k = 0; k < rest.size(); k += 2)
-      keyed.push_back({b->ncells[rest[k]], make_int2(rest[k], k + 1 < rest.size() ? rest[k + 1] : -1)});
-    std::stable_sort(keyed.begin(), keyed.end(),
-                     [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) {
-                       return x.first > y.first;
-                     });
-    for (auto& x : keyed) items.push_back(x.second);
-    if (cudaMemcpy(b->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) !=
+  if (n_items > 0) {
+    if (cudaMemcpy(b->items, items.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return ppml_fail(PPML_E_CUDA, "batch items copy: %s", cudaGetErrorString(cudaGetLastError()));
-  } else if (cudaMemcpy(b->order, rest.data(), sizeof(int) * rest.size(),
+  } else if (cudaMemcpy(b->order, order.data(), sizeof(int) * b->n_inst,
                         cudaMemcpyHostToDevice) != cudaSuccess) {
     return ppml_fail(PPML_E_CUDA, "batch order copy: %s", cudaGetErrorString(cudaGetLastError()));
   }
-  b->n_items = (int)items.size();
-  b->n_split = (int)split.size();
+  b->n_items = n_items;
+  b->n_split = n_split;
   b->nlmax = nlmax;
   b->nmax = nmax;
   b->smem = smem;
@@ -129,6 +123,42 @@ int check_state(void* const state[4]) {
   return PPML_OK;
 }
 }  // namespace
+
+extern "C" int ppml_batch_plan(int n_inst, const int* ncells, int split_min, int* items,
+                               int* n_items, int* order) {
+  ppml_clear_error();
+  if (n_inst < 1 || !ncells || !items || !n_items)
+    return ppml_fail(PPML_E_INVAL, "need n_inst >= 1 and non-NULL ncells, items, n_items");
+  if (split_min != 0 && split_min < kSplitFloor)
+    return ppml_fail(PPML_E_INVAL, "split_min = %d: 0 (no split) or >= %d", split_min, kSplitFloor);
+  std::vector<int> split, rest;
+  for (int i = 0; i < n_inst; i++)
+    (split_min > 0 && ncells[i] >= split_min ? split : rest).push_back(i);
+  auto by_size = [&](int x, int y) { return ncells[x] > ncells[y]; };
+  std::stable_sort(split.begin(), split.end(), by_size);
+  std::stable_sort(rest.begin(), rest.end(), by_size);
+  *n_items = 0;
+  if (split.empty()) {
+    if (order)
+      for (int k = 0; k < n_inst; k++) order[k] = rest[k];
+    return PPML_OK;
+  }
+  // (size of the item's largest instance, a, b), largest first; ties keep split items
+  // ahead of whole ones and the instances' order
+  std::vector<std::pair<int, std::pair<int, int>>> keyed;
+  for (int i : split) keyed.push_back({ncells[i], {i, kItemSplit}});
+  for (size_t k = 0; k < rest.size(); k += 2)
+    keyed.push_back({ncells[rest[k]], {rest[k], k + 1 < rest.size() ? rest[k + 1] : -1}});
+  std::stable_sort(keyed.begin(), keyed.end(),
+                   [](const std::pair<int, std::pair<int, int>>& x,
+                      const std::pair<int, std::pair<int, int>>& y) { return x.first > y.first; });
+  for (size_t k = 0; k < keyed.size(); k++) {
+    items[2 * k] = keyed[k].second.first;
+    items[2 * k + 1] = keyed[k].second.second;
+  }
+  *n_items = (int)keyed.size();
+  return PPML_OK;
+}
 
 extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
                                const double* t_end, double gamma, double cfl,

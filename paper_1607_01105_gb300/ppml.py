@@ -30,7 +30,7 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
             "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak",
-            "ppml_batch_set_split")
+            "ppml_batch_set_split", "ppml_batch_plan")
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -78,6 +78,9 @@ _lib.ppml_batch_tune.argtypes = [_vp, ctypes.c_void_p * 4, ctypes.c_int, ctypes.
                                  ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_batch_set_threads.argtypes = [_vp, ctypes.c_int]
 _lib.ppml_batch_set_split.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_batch_plan.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)]
 _lib.ppml_fourier_amplitudes.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(State), ctypes.POINTER(State),
@@ -342,6 +345,19 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def batch_plan(ncells, split_min):
+    """Work plan of ppml_batch_plan: (items as a list of (a, b), order or None)."""
+    n = len(ncells)
+    cells = (ctypes.c_int * n)(*[int(x) for x in ncells])
+    items = (ctypes.c_int * (2 * n))()
+    order = (ctypes.c_int * n)()
+    k = ctypes.c_int()
+    _check(_lib.ppml_batch_plan(n, cells, int(split_min), items, ctypes.byref(k), order))
+    if k.value == 0:
+        return [], list(order)
+    return [(items[2 * i], items[2 * i + 1]) for i in range(k.value)], None
 
 
 def fma_peak(dtype: int, iters: int, stream=None) -> float:

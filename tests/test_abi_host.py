@@ -83,3 +83,41 @@ def test_invalid_descriptors_rejected_on_host(built):
     assert lib.ppml_free_grid(None) == ppml.PPML_OK
     assert lib.ppml_poisson_isolated(None, None, None, 1.0, 0, None) == ppml.PPML_E_INVAL
     assert lib.ppml_poisson_periodic(None, None, None, 1.0, None) == ppml.PPML_E_INVAL
+
+
+def test_batch_work_plan_on_host(built):
+    """The batch work plan (host logic, no device call): every instance appears exactly once;
+    instances of at least split_min cells, and only they, are split over a CTA pair; the
+    items come largest first by their largest instance, whole instances paired in order of
+    size; with no split the plan is one CTA per instance, largest first (stable).  Invalid
+    thresholds are rejected."""
+    import numpy as np
+    from paper_1607_01105_gb300 import ppml
+    rng = np.random.default_rng(5)
+    cells = [int(x) for x in 2 * rng.integers(64, 2049, size=101)]
+    for split_min in (1024, 2000, 3000, 64):
+        items, order = ppml.batch_plan(cells, split_min)
+        assert order is None and items
+        seen = []
+        for a, b in items:
+            seen.append(a)
+            if b == -2:
+                assert cells[a] >= split_min
+            else:
+                assert cells[a] < split_min
+                if b >= 0:
+                    assert cells[b] < split_min and cells[b] <= cells[a]
+                    seen.append(b)
+        assert sorted(seen) == list(range(len(cells)))
+        keys = [cells[a] for a, _ in items]
+        assert keys == sorted(keys, reverse=True)
+        whole = [x for a, b in items if b != -2 for x in (a, b) if x >= 0]
+        assert [cells[x] for x in whole] == sorted((cells[x] for x in whole), reverse=True)
+        assert sum(1 for _, b in items if b == -1) <= 1
+    items, order = ppml.batch_plan(cells, 10 ** 6)  # nothing large enough: one CTA each
+    assert items == [] and order == sorted(range(len(cells)), key=lambda i: (-cells[i], i))
+    items, order = ppml.batch_plan(cells, 0)
+    assert items == [] and order == sorted(range(len(cells)), key=lambda i: (-cells[i], i))
+    for bad in (10, -1):
+        with pytest.raises(ppml.PPMLError):
+            ppml.batch_plan(cells, bad)
