@@ -80,6 +80,8 @@ def lib():
         _lib.oracle_face_lambda.restype = ctypes.c_double
         _lib.oracle_energy_correction.argtypes = [_dp, ctypes.c_double]
         _lib.oracle_energy_correction.restype = ctypes.c_int
+        _lib.oracle_face_velocities.argtypes = [ctypes.POINTER(_Desc), _P6, ctypes.c_int, _dp]
+        _lib.oracle_face_velocities.restype = ctypes.c_int
     return _lib
 
 
@@ -213,6 +215,24 @@ def energy_correction(u6, rho_vac):
     a = np.ascontiguousarray(u6, dtype=np.float64).copy()
     code = lib().oracle_energy_correction(a.ctypes.data_as(_dp), rho_vac)
     return a, code
+
+
+def face_velocities(grid: Grid, u_star, axis: int):
+    """S5 alone: the face velocities v hat along `axis` of the state u_star (the 9-point
+    template of eq. veltemplate and the sqrt(rho) weights of eq.
+    modspaceaveragevelocitylagrange), as the Lagrangian stage forms them.  Returns an
+    array of shape (nz, ny, nx) with the axis extended by one: entry c along the axis is
+    the face between cells c-1 and c."""
+    shape = (grid.n[2], grid.n[1], grid.n[0])
+    uin = _as_fields(u_star, shape)
+    m = [int(grid.n[0]), int(grid.n[1]), int(grid.n[2])]
+    m[axis] += 1
+    out = np.empty((m[2], m[1], m[0]))
+    d = grid.desc()
+    rc = lib().oracle_face_velocities(ctypes.byref(d), _ptrs(uin), int(axis), out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise ValueError("face velocities need an active axis")
+    return out
 
 
 def primitives(grid: Grid, u):

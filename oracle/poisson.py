@@ -54,7 +54,7 @@ def solve_periodic(rho, h, G=1.0):
     den[0, 0, 0] = 1.0
     phik = -(2.0 / 3.0) * math.pi * G * h * h * sigma / den
     phik[0, 0, 0] = 0.0
-    return np.fft.irfftn(phik, s=rho.shape)
+    return np.fft.irfftn(phik, s=rho.shape, axes=(0, 1, 2))
 
 
 def apply_stencil(phi):

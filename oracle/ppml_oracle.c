@@ -405,6 +405,58 @@ static int eulerian_stage(const gshape* s, const oracle_desc* d, double* const U
 
 /* -------------------------------------------------------------- Lagrangian stage */
 
+/* S5 along axis a on ghost-filled U* (padded): v_a = m_a / rho on every padded cell,
+ * the 9-point template v tilde in the plane normal to a (eq. veltemplate: 1/16 at the
+ * four corners, 1/8 at the four edge neighbours, 1/4 at the cell itself; the cell's own
+ * v in the one-point variant) on every cell whose transverse neighbours exist (a
+ * single-cell transverse axis uses the cell itself, which makes the template the 1D / 2D
+ * marginal), and the sqrt(rho)-weighted face velocity v hat of eq.
+ * modspaceaveragevelocitylagrange at faces c+1/2, c in [NG-1, NG+n-1], of every interior
+ * line, stored at the index of the face's left cell. */
+static void face_velocities(const gshape* s, const oracle_desc* d, double* const Us[NFIELD],
+                            int a, double* vel, double* vt, double* vhat) {
+  size_t nc = s->cells;
+  int b = (a + 1) % 3, cax = (a + 2) % 3; /* template roles (eq. veltemplate) */
+  int li, lo;                             /* loop order (memory strides) */
+  transverse(a, &li, &lo);
+  size_t st = axis_stride(s, a), sb = axis_stride(s, b), sc = axis_stride(s, cax);
+  int N = s->N[a];
+  for (size_t c = 0; c < nc; c++) vel[c] = Us[F_MX + a][c] / Us[F_RHO][c];
+#pragma omp parallel for schedule(static)
+  for (int io = 0; io < s->N[lo]; io++)
+    for (int ii = 0; ii < s->N[li]; ii++) {
+      int idx[3];
+      idx[lo] = io; idx[li] = ii;
+      int ib = idx[b], ic = idx[cax];
+      int bm = (s->n[b] == 1) ? 0 : 1, cm = (s->n[cax] == 1) ? 0 : 1;
+      if (ib - bm < 0 || ib + bm >= s->N[b] || ic - cm < 0 || ic + cm >= s->N[cax]) continue;
+      for (int ia = 0; ia < N; ia++) {
+        idx[a] = ia;
+        size_t g = gidx(s, idx[0], idx[1], idx[2]);
+        size_t db = sb * (size_t)bm, dc = sc * (size_t)cm;
+        if (d->flags & ORACLE_VHAT_1PT) {
+          vt[g] = vel[g];
+          continue;
+        }
+        double corners = vel[g + db + dc] + vel[g + db - dc] + vel[g - db + dc] + vel[g - db - dc];
+        double edges = vel[g + db] + vel[g - db] + vel[g + dc] + vel[g - dc];
+        vt[g] = corners / 16.0 + edges / 8.0 + vel[g] / 4.0;
+      }
+    }
+#pragma omp parallel for schedule(static)
+  for (int io = s->g[lo]; io < s->g[lo] + s->n[lo]; io++)
+    for (int ii = s->g[li]; ii < s->g[li] + s->n[li]; ii++) {
+      int idx[3];
+      idx[a] = 0; idx[lo] = io; idx[li] = ii;
+      size_t base = gidx(s, idx[0], idx[1], idx[2]);
+      for (int c = NG - 1; c <= NG + s->n[a] - 1; c++) {
+        size_t gl = base + st * c, gr = gl + st;
+        double sl = sqrt(Us[F_RHO][gl]), sr = sqrt(Us[F_RHO][gr]);
+        vhat[gl] = (vt[gr] * sr + vt[gl] * sl) / (sr + sl);
+      }
+    }
+}
+
 /* S5-S7 on ghost-filled U* (padded); writes U^{n+1} into Un (padded, interior only). */
 static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const Us[NFIELD],
                             double* const Un[NFIELD], double tau) {
@@ -417,50 +469,12 @@ static int lagrangian_stage(const gshape* s, const oracle_desc* d, double* const
 
   for (int a = 0; a < 3; a++) {
     if (s->n[a] == 1) continue;
-    int b = (a + 1) % 3, cax = (a + 2) % 3; /* template roles (eq. veltemplate) */
-    int li, lo;                             /* loop order (memory strides) */
+    int li, lo; /* loop order (memory strides) */
     transverse(a, &li, &lo);
-    size_t st = axis_stride(s, a), sb = axis_stride(s, b), sc = axis_stride(s, cax);
+    size_t st = axis_stride(s, a);
     int N = s->N[a];
     double rk = tau / d->h[a];
-    for (size_t c = 0; c < nc; c++) vel[c] = Us[F_MX + a][c] / Us[F_RHO][c];
-    /* S5: 9-point template in the plane normal to a, on cells whose transverse
-     * neighbours exist (single-cell transverse axes use the cell itself, which makes
-     * the template reduce to the 1D / 2D marginals). */
-#pragma omp parallel for schedule(static)
-    for (int io = 0; io < s->N[lo]; io++)
-      for (int ii = 0; ii < s->N[li]; ii++) {
-        int idx[3];
-        idx[lo] = io; idx[li] = ii;
-        int ib = idx[b], ic = idx[cax];
-        int bm = (s->n[b] == 1) ? 0 : 1, cm = (s->n[cax] == 1) ? 0 : 1;
-        if (ib - bm < 0 || ib + bm >= s->N[b] || ic - cm < 0 || ic + cm >= s->N[cax]) continue;
-        for (int ia = 0; ia < N; ia++) {
-          idx[a] = ia;
-          size_t g = gidx(s, idx[0], idx[1], idx[2]);
-          size_t db = sb * (size_t)bm, dc = sc * (size_t)cm;
-          if (d->flags & ORACLE_VHAT_1PT) {
-            vt[g] = vel[g];
-            continue;
-          }
-          double corners = vel[g + db + dc] + vel[g + db - dc] + vel[g - db + dc] + vel[g - db - dc];
-          double edges = vel[g + db] + vel[g - db] + vel[g + dc] + vel[g - dc];
-          vt[g] = corners / 16.0 + edges / 8.0 + vel[g] / 4.0;
-        }
-      }
-    /* faces along a: v hat at c+1/2 for the interior lines */
-#pragma omp parallel for schedule(static)
-    for (int io = s->g[lo]; io < s->g[lo] + s->n[lo]; io++)
-      for (int ii = s->g[li]; ii < s->g[li] + s->n[li]; ii++) {
-        int idx[3];
-        idx[a] = 0; idx[lo] = io; idx[li] = ii;
-        size_t base = gidx(s, idx[0], idx[1], idx[2]);
-        for (int c = NG - 1; c <= NG + s->n[a] - 1; c++) {
-          size_t gl = base + st * c, gr = gl + st;
-          double sl = sqrt(Us[F_RHO][gl]), sr = sqrt(Us[F_RHO][gr]);
-          vhat[gl] = (vt[gr] * sr + vt[gl] * sl) / (sr + sl);
-        }
-      }
+    face_velocities(s, d, Us, a, vel, vt, vhat); /* S5 */
     /* S6: fluxes of every field; S7 accumulation */
 #pragma omp parallel
     {
@@ -597,6 +611,43 @@ double oracle_face_lambda(double rl, double rr, double pl, double pr, double gam
 }
 
 int oracle_energy_correction(double* u6, double rho_vac) { return energy_correction(u6, rho_vac); }
+
+/* S5 alone: the face velocities v hat along axis a (0..2, an active axis) of the state
+ * u_star (six interior-only arrays, ghost-filled here with the descriptor's boundaries).
+ * vhat_out holds the faces of every line along a: (n_a + 1) faces, face c between
+ * interior cells c-1 and c, the other axes as in the state (x fastest).  Returns 0, or -1
+ * for an inactive axis or a failed allocation. */
+int oracle_face_velocities(const oracle_desc* d, double* const u_star[NFIELD], int a,
+                           double* vhat_out) {
+  if (a < 0 || a > 2 || d->n[a] == 1) return -1;
+  gshape s = make_shape(d);
+  double* Us[NFIELD];
+  for (int f = 0; f < NFIELD; f++) {
+    Us[f] = (double*)calloc(s.cells, sizeof(double));
+    if (!Us[f]) return -1;
+    scatter_interior(&s, u_star[f], Us[f]);
+    fill_ghosts(&s, d, Us[f], f);
+  }
+  double* vel = (double*)xmalloc(s.cells * sizeof(double));
+  double* vt = (double*)xmalloc(s.cells * sizeof(double));
+  double* vhat = (double*)xmalloc(s.cells * sizeof(double));
+  face_velocities(&s, d, Us, a, vel, vt, vhat);
+  int m[3] = {d->n[0], d->n[1], d->n[2]};
+  m[a] += 1;
+  for (int k = 0; k < m[2]; k++)
+    for (int j = 0; j < m[1]; j++)
+      for (int i = 0; i < m[0]; i++) {
+        int c[3] = {i, j, k};
+        c[a] -= 1; /* face c[a] + 1/2 of interior cell c[a] - 1 */
+        vhat_out[(size_t)i + (size_t)m[0] * ((size_t)j + (size_t)m[1] * (size_t)k)] =
+            vhat[gidx(&s, c[0] + s.g[0], c[1] + s.g[1], c[2] + s.g[2])];
+      }
+  free(vel);
+  free(vt);
+  free(vhat);
+  for (int f = 0; f < NFIELD; f++) free(Us[f]);
+  return 0;
+}
 
 /* One full step.  u_in, u_out: six interior-only arrays each (may alias: the output is
  * written only at the end).  u_star (optional, may be NULL): receives U* interior.

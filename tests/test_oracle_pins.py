@@ -549,6 +549,136 @@ def test_nine_point_template_reduces_grid_alignment_artifacts():
     assert res[oracle.VHAT_1PT] > 1.15 * res[0], res
 
 
+def _delta_state(n, axis, centre, delta=1.0):
+    """Uniform gas at rest (rho = 1, p = 1) with momentum `delta` along `axis` in one cell."""
+    shape = (n[2], n[1], n[0])
+    rho = np.ones(shape)
+    m = [np.zeros(shape) for _ in range(3)]
+    m[axis][centre[2], centre[1], centre[0]] = delta
+    return [rho, m[0], m[1], m[2], np.full(shape, 2.5), np.full(shape, 2.5)]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_velocity_template_weights_on_a_delta(axis):
+    """Eq. veltemplate: the transverse template puts 1/16 on the four corner neighbours,
+    1/8 on the four edge neighbours and 1/4 on the cell itself (the weights the paper
+    prints, tests/golden/paper_values.json); with uniform density the face velocity of eq.
+    modspaceaveragevelocitylagrange is the mean of the two adjacent template values.  A
+    delta of v_a in one cell therefore gives v hat = w/2 on the two faces of that cell's
+    line and of its transverse neighbours' lines (w the template weight of the line) and
+    zero on every other face.  Swapping the corner and edge weights (which still sum to
+    one) or the template's transverse axes fails this."""
+    w = GOLDEN["velocity_template"]
+    n, c = (7, 8, 9), (3, 4, 4)
+    g = oracle.Grid(n, (1.0, 1.0, 1.0), 1.4, (1,) * 6, 0.2)
+    vh = oracle.face_velocities(g, _delta_state(n, axis, c), axis)
+    expect = np.zeros_like(vh)
+    tr = [a for a in range(3) if a != axis]
+    for db in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            k = abs(db) + abs(dc)
+            wt = w["centre"] if k == 0 else (w["edge"] if k == 1 else w["corner"])
+            for face in (c[axis], c[axis] + 1):  # the two faces of the delta's cell
+                idx = list(c)
+                idx[axis] = face
+                idx[tr[0]] += db
+                idx[tr[1]] += dc
+                expect[idx[2], idx[1], idx[0]] = 0.5 * wt
+    assert np.allclose(vh, expect, rtol=0, atol=1e-15)
+    assert vh.sum() == pytest.approx(1.0, abs=1e-14)  # the weights sum to one per face plane
+
+
+def test_velocity_template_one_point_and_lower_dimensional_marginals():
+    """The one-point variant (Sec. 1.3) takes the cell's own v; on a 2D grid the template
+    of the remaining transverse axis is the marginal of the 9-point one (1/4, 1/2, 1/4:
+    the corner and edge weights summed over the inactive axis) and in 1D it is v itself."""
+    n, c = (9, 9, 1), (4, 4, 0)
+    g = oracle.Grid(n, (1.0, 1.0, 1.0), 1.4, (1, 1, 1, 1, 0, 0), 0.2)
+    vh = oracle.face_velocities(g, _delta_state(n, 0, c), 0)[0]
+    w = GOLDEN["velocity_template"]
+    side, mid = 2 * w["corner"] + w["edge"], 2 * w["edge"] + w["centre"]
+    assert (side, mid) == (0.25, 0.5)
+    expect = np.zeros_like(vh)
+    for face in (4, 5):
+        expect[3, face] = expect[5, face] = 0.5 * side
+        expect[4, face] = 0.5 * mid
+    assert np.allclose(vh, expect, rtol=0, atol=1e-15)
+    g1 = oracle.Grid(n, (1.0, 1.0, 1.0), 1.4, (1, 1, 1, 1, 0, 0), 0.2, flags=oracle.VHAT_1PT)
+    vh1 = oracle.face_velocities(g1, _delta_state(n, 0, c), 0)[0]
+    expect1 = np.zeros_like(vh1)
+    expect1[4, 4] = expect1[4, 5] = 0.5
+    assert np.allclose(vh1, expect1, rtol=0, atol=1e-15)
+    n1 = (9, 1, 1)
+    g2 = oracle.Grid(n1, (1.0, 1.0, 1.0), 1.4, (1, 1, 0, 0, 0, 0), 0.2)
+    vh2 = oracle.face_velocities(g2, _delta_state(n1, 0, (4, 0, 0)), 0)[0, 0]
+    assert np.allclose(vh2, [0, 0, 0, 0, 0.5, 0.5, 0, 0, 0, 0], rtol=0, atol=1e-15)
+
+
+def test_face_velocity_roe_weights():
+    """Eq. modspaceaveragevelocitylagrange: v hat = (v_i sqrt(rho_i) + v_i+1 sqrt(rho_i+1)) /
+    (sqrt(rho_i) + sqrt(rho_i+1)).  A 1D line with rho = 1 | 4 and v = 0.3 | 0.9 gives
+    (0.3 + 2 * 0.9) / 3 = 0.7 at the interface (swapped weights: 0.5) and the adjacent
+    cells' own v elsewhere."""
+    n = (12, 1, 1)
+    rho = np.where(np.arange(12) < 6, 1.0, 4.0)
+    v = np.where(np.arange(12) < 6, 0.3, 0.9)
+    z = np.zeros(12)
+    u = [rho[None, None], (rho * v)[None, None], z[None, None], z[None, None],
+         np.full((1, 1, 12), 3.0), np.full((1, 1, 12), 1.0)]
+    g = oracle.Grid(n, (1.0, 1.0, 1.0), 1.4, (0,) * 6, 0.2)
+    vh = oracle.face_velocities(g, u, 0)[0, 0]
+    assert vh[6] == pytest.approx(0.7, abs=1e-15)
+    assert np.allclose(vh[:6], 0.3, rtol=0, atol=1e-15)
+    assert np.allclose(vh[7:], 0.9, rtol=0, atol=1e-15)
+
+
+def _gravity_case(m0, gvec, tau=0.01, n=12, rho=1.3, p=1.0, gamma=1.4):
+    """Uniform gas (momentum m0) in the linear potential Phi = g . x on an n^3 outflow grid:
+    one oracle step.  Returns (input, output) restricted to cells at least 4 from every
+    face, which no boundary value reaches in either stage."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    zz, yy, xx = np.meshgrid(x, x, x, indexing="ij")
+    phi = gvec[0] * xx + gvec[1] * yy + gvec[2] * zz
+    shape = (n, n, n)
+    e = p / (gamma - 1.0)
+    ke = 0.5 * sum(mc * mc for mc in m0) / rho
+    u = [np.full(shape, rho)] + [np.full(shape, mc) for mc in m0] + \
+        [np.full(shape, e + ke), np.full(shape, e)]
+    g = oracle.Grid((n, n, n), (h, h, h), gamma, (0,) * 6, 0.2, rho_mean=rho)
+    out, _ = oracle.step(g, u, tau, phi=phi)
+    core = (slice(4, n - 4),) * 3
+    return [f[core] for f in u], [f[core] for f in out]
+
+
+def test_gravity_source_of_gas_at_rest():
+    """Model equations, source terms -rho grad Phi (momentum) and -rho v . grad Phi (total
+    energy), central difference of Phi (reading G16): uniform gas at rest in Phi = g . x
+    gains momentum -tau rho g in one step, exactly up to rounding, and keeps its total
+    energy (the flow it gains is uniform, so the Lagrangian fluxes cancel).  A flipped sign
+    or a missing 1/2 in the central difference fails."""
+    gvec, tau, rho = (0.3, -0.2, 0.5), 0.01, 1.3
+    uin, uout = _gravity_case((0.0, 0.0, 0.0), gvec, tau=tau, rho=rho)
+    assert np.allclose(uout[0], rho, rtol=1e-15, atol=0)
+    for a in range(3):
+        assert np.allclose(uout[1 + a], -tau * rho * gvec[a], rtol=1e-10, atol=0), a
+    assert np.allclose(uout[4], uin[4], rtol=1e-15, atol=0)
+    # the energy correction takes the new kinetic energy from the internal energy
+    ke = 0.5 * tau * tau * rho * sum(gc * gc for gc in gvec)
+    assert np.allclose(uout[5], uin[5] - ke, rtol=1e-12, atol=0)
+
+
+def test_gravity_source_of_moving_gas():
+    """With uniform momentum m the total energy changes by -tau m . g in one step (the
+    work of gravity on the flow, taken from U^n), the momentum by -tau rho g."""
+    m0, gvec, tau, rho = (0.4, 0.1, -0.3), (0.3, -0.2, 0.5), 0.01, 1.3
+    uin, uout = _gravity_case(m0, gvec, tau=tau, rho=rho)
+    work = -tau * sum(mc * gc for mc, gc in zip(m0, gvec))
+    assert np.allclose(uout[4] - uin[4], work, rtol=1e-9, atol=0)
+    for a in range(3):
+        assert np.allclose(uout[1 + a], m0[a] - tau * rho * gvec[a], rtol=1e-12, atol=0), a
+
+
 # ------------------------------------------------------- reflecting walls (NEXT)
 
 def _local_peaks(q, x, order=40):
