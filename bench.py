@@ -12,11 +12,12 @@ Under torchrun with N > 1 each rank advances its own replica (the grid is not sp
 across GPUs); value = all ranks' cell-updates / max-over-ranks time.
 
 The line's "configs" object times the other workloads on the GPU beside the headline: the
-1D Sod run to t = 0.2 (launch-bound) and the planar Sod 128^3 in FP32 and FP64, and with
---all-configs also the 512^3 galactic disk (hydro steps with gravity; the Poisson solve
-between them untimed).  --cpu-table instead times the FP64 oracle, as it stands, on a
-bounded sample of every workload with one thread and with all host cores (no GPU use) and
-prints that table as its one JSON line.
+1D Sod run to t = 0.2 (launch-bound), the planar Sod 128^3 in FP32 and FP64, and the 512^3
+galactic disk (hydro steps with gravity; the Poisson solve between them untimed; a few
+steps by default, --steps of them with --all-configs).  "fp32_double_float" times the same
+256^3 step on a double-float state (rho, m, rho E as float pairs).  --cpu-table instead
+times the FP64 oracle, as it stands, on a bounded sample of every workload with one thread
+and with all host cores (no GPU use) and prints that table as its one JSON line.
 """
 from __future__ import annotations
 
@@ -237,7 +238,7 @@ def cpu_table(args):
     return 0
 
 
-def gpu_configs(args, dev, stream, barrier, with_disk):
+def gpu_configs(args, dev, stream, barrier, disk_steps):
     """GPU timings of the other workloads through the same C ABI (CUDA events on the
     launching stream): the 1D Sod 256 run to t = 0.2 (the steps of the full run, counted
     in an untimed run first, then launched back to back from t = 0 on a fresh grid), the
@@ -327,7 +328,7 @@ def gpu_configs(args, dev, stream, barrier, with_disk):
     out["planar_sod_128"] = dict(res, unit="Mcell-updates/s",
                                  workload="planar Sod 128^3, split on x = 0.5, outflow in x, "
                                           "periodic in y and z, CFL 0.2")
-    if with_disk:
+    if disk_steps > 0:
         pb = inputs.galactic_disk(n=512)
         dtype = ppml.PPML_F32
         u = ppml.to_device(pb.u, dtype)
@@ -335,8 +336,8 @@ def gpu_configs(args, dev, stream, barrier, with_disk):
         g = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u)
         halo = torch.as_tensor(pb.extra["phi_halo"].ravel()).to(dev, torch.float32)
         phi = torch.empty_like(u[0])
-        ms, steps = 0.0, args.steps
-        for k in range(args.warmup + steps):
+        ms, steps = 0.0, disk_steps
+        for k in range(min(args.warmup, 3) + steps):
             g.poisson_periodic(u[0], phi, 1.0)
             phi.add_(halo)
             e0, e1 = events()
@@ -345,7 +346,7 @@ def gpu_configs(args, dev, stream, barrier, with_disk):
             g.step_phi(u, v, phi, 0.0)
             e1.record(stream)
             barrier()
-            if k >= args.warmup:
+            if k >= min(args.warmup, 3):
                 ms += e0.elapsed_time(e1)
             u, v = v, u
         g.close()
@@ -462,8 +463,23 @@ def main():
                         "instances": int(bb.ncells.size), "cells": int(bb.cells),
                         "done": int(sum(1 for t, te in zip(bt_t, bb.t_end) if t >= te)),
                         "threads": b_threads, "tune_ms": {str(k): v for k, v in b_tune.items()}}
+    # the same FP32 batch on a double-float state (rho, m, rho E as float pairs)
+    bst = [torch.as_tensor(x).to(dev, torch.float32) for x in bb.u]
+    blo = [(torch.as_tensor(x).to(dev) - y.double()).float() for x, y in zip(bb.u[:3], bst[:3])]
+    batch_df = ppml.Batch(bb.ncells, bb.h, bb.t_end, bb.gamma, bb.cfl, ppml.PPML_F32)
+    batch_df.set_threads(b_threads)
+    barrier()
+    b0.record(stream)
+    batch_df.step(bst, 1 << 30, lo=blo)
+    b1.record(stream)
+    barrier()
+    _, bdf_steps = batch_df.status()
+    results["batch_df"] = {"ms": max_over_ranks_(b0.elapsed_time(b1)),
+                           "updates": float(np.dot(bb.ncells.astype(np.float64),
+                                                   np.asarray(bdf_steps, dtype=np.float64)))}
     batch.close()
-    del bst
+    batch_df.close()
+    del bst, blo
     # the same batch in FP64 (its own autotuned CTA size)
     bst64 = [torch.as_tensor(x).to(dev, torch.float64) for x in bb.u]
     batch64 = ppml.Batch(bb.ncells, bb.h, bb.t_end, bb.gamma, bb.cfl, ppml.PPML_F64)
@@ -480,12 +496,15 @@ def main():
                                                   np.asarray(b64_steps, dtype=np.float64)))}
     batch64.close()
     del bst64
-    for dtype, name in ((ppml.PPML_F32, "f32"), (ppml.PPML_F64, "f64")):
+    for dtype, name, df in ((ppml.PPML_F32, "f32", False), (ppml.PPML_F32, "f32df", True),
+                            (ppml.PPML_F64, "f64", False)):
         elt = 4 if dtype == ppml.PPML_F32 else 8
-        u = ppml.to_device(pb.u, dtype)
+        u = ppml.to_device(pb.u, dtype, lo=df)
         v = [torch.empty_like(x) for x in u]
         grid = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u)
         steps = args.steps if dtype == ppml.PPML_F32 else max(3, args.steps // 10)
+        if df:
+            steps = max(3, args.steps // 2)
         for _ in range(args.warmup):
             grid.step(u, v, 0.0)
             u, v = v, u
@@ -513,7 +532,7 @@ def main():
         # memory, all inside the timed region.  Uploads and downloads run on their own
         # streams with two device buffers each, so the upload of step k overlaps the step
         # and the download of step k-1 (events order every reuse of a buffer).
-        if dtype == ppml.PPML_F32:
+        if name == "f32":
             hin = [x.cpu().pin_memory() for x in u]
             hout = [[torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in hin]
                     for _ in range(2)]
@@ -524,37 +543,39 @@ def main():
             ev_step = [torch.cuda.Event() for _ in range(2)]
             ev_down = [torch.cuda.Event() for _ in range(2)]
             e_steps = max(6, steps // 2)
-            torch.cuda.synchronize()
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s_up.wait_stream(stream)
-            s_down.wait_stream(stream)
-            for k in range(e_steps):
-                i = k % 2
-                if k >= 2:
-                    s_up.wait_event(ev_step[i])  # step k-2 has read dev_in[i]
-                with torch.cuda.stream(s_up):
-                    for dst, src in zip(dev_in[i], hin):
-                        dst.copy_(src, non_blocking=True)
-                ev_up[i].record(s_up)
-                stream.wait_event(ev_up[i])
-                if k >= 2:
-                    stream.wait_event(ev_down[i])  # step k-2's result has left dev_out[i]
-                grid.step(dev_in[i], dev_out[i], 0.0, stream=stream)
-                ev_step[i].record(stream)
-                s_down.wait_event(ev_step[i])
-                with torch.cuda.stream(s_down):
-                    for dst, src in zip(hout[i], dev_out[i]):
-                        dst.copy_(src, non_blocking=True)
-                ev_down[i].record(s_down)
-            stream.wait_stream(s_up)
-            stream.wait_stream(s_down)
-            e1.record(stream)
-            barrier()
-            ems = max_over_ranks_(e0.elapsed_time(e1))
-            results["e2e"] = {"ms": ems, "steps": e_steps,
+            e2e_ms = []
+            for _rep in range(3):  # three end-to-end runs: the median is reported
+                torch.cuda.synchronize()
+                barrier()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s_up.wait_stream(stream)
+                s_down.wait_stream(stream)
+                for k in range(e_steps):
+                    i = k % 2
+                    if k >= 2:
+                        s_up.wait_event(ev_step[i])  # step k-2 has read dev_in[i]
+                    with torch.cuda.stream(s_up):
+                        for dst, src in zip(dev_in[i], hin):
+                            dst.copy_(src, non_blocking=True)
+                    ev_up[i].record(s_up)
+                    stream.wait_event(ev_up[i])
+                    if k >= 2:
+                        stream.wait_event(ev_down[i])  # step k-2's result has left dev_out[i]
+                    grid.step(dev_in[i], dev_out[i], 0.0, stream=stream)
+                    ev_step[i].record(stream)
+                    s_down.wait_event(ev_step[i])
+                    with torch.cuda.stream(s_down):
+                        for dst, src in zip(hout[i], dev_out[i]):
+                            dst.copy_(src, non_blocking=True)
+                    ev_down[i].record(s_down)
+                stream.wait_stream(s_up)
+                stream.wait_stream(s_down)
+                e1.record(stream)
+                barrier()
+                e2e_ms.append(max_over_ranks_(e0.elapsed_time(e1)))
+            results["e2e"] = {"ms": statistics.median(e2e_ms), "ms_runs": e2e_ms, "steps": e_steps,
                               "h2d": 6 * cells * elt, "d2h": 6 * cells * elt}
             # the same step mid-run: advance (untimed) toward half the time at which the blast
             # radius reaches 0.4, at most 4000 steps, then time as many steps again
@@ -581,14 +602,14 @@ def main():
         del u, v
         torch.cuda.empty_cache()
 
-    configs = gpu_configs(args, dev, stream, barrier, args.all_configs)
+    configs = gpu_configs(args, dev, stream, barrier, args.steps if args.all_configs else 6)
     # measured FMA throughput of the device (the arithmetic roofline denominators)
     fma_peak = {"f32": ppml.fma_peak(ppml.PPML_F32, 200000, stream=stream),
                 "f64": ppml.fma_peak(ppml.PPML_F64, 4000, stream=stream)}
 
     if rank == 0:
         peak, peak_kind = load_peaks()
-        r32, r64 = results["f32"], results["f64"]
+        r32, r64, rdf = results["f32"], results["f64"], results["f32df"]
         value = whole_job_rate(cells, r32["steps"], world, r32["ms"])
         v64 = whole_job_rate(cells, r64["steps"], world, r64["ms"])
         keul, klag, kfin = r32["kernel_ms"]
@@ -601,6 +622,7 @@ def main():
         step_bytes = (BYTES_EUL[4] + BYTES_LAG[4]) * cells
         e2e = results["e2e"]
         e2e_val = whole_job_rate(cells, e2e["steps"], world, e2e["ms"])
+        e2e_runs = [whole_job_rate(cells, e2e["steps"], world, x) for x in e2e["ms_runs"]]
         line = {
             "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
             "steps": r32["steps"], "warmup": args.warmup, "ms_per_step": r32["ms"] / r32["steps"],
@@ -615,6 +637,8 @@ def main():
             "roofline": {"bound": "alu", "kernel": "lagrangian_tile<float>",
                          "achieved": lag_ops, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": lag_ops / alu_peak,
+                         "hbm_frac": lag_gbs / peak,
+                         "hbm_achieved_gbs": lag_gbs,
                          "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {clk:.0f} MHz, "
                                        "one operation per lane per clock (FMA counted once)",
                          "algorithmic_ops_per_cell": OPS_LAG,
@@ -653,6 +677,9 @@ def main():
                                        / (results["batch64"]["ms"] * 1e-3) / 1e6,
                                        "ms": results["batch64"]["ms"],
                                        "cta_threads": results["batch64"]["threads"]},
+                              "double_float": {"value": results["batch_df"]["updates"]
+                                               / (results["batch_df"]["ms"] * 1e-3) / 1e6,
+                                               "ms": results["batch_df"]["ms"]},
                               "tune_ms_20_steps": results["batch"]["tune_ms"],
                               "workload": "512 uneven 1D Riemann problems (128..4096 cells), "
                                           "each run to its own end time in one persistent launch"},
@@ -663,7 +690,15 @@ def main():
                         "note": "same FP32 step timed after advancing toward half the end time "
                                 "(at most 4000 steps; t reached is given)"},
             "e2e": {"value": e2e_val, "unit": "Mcell-updates/s",
-                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                    "runs": e2e_runs, "min": min(e2e_runs), "stat": "median of 3 runs"},
+            "fp32_double_float": {
+                "value": whole_job_rate(cells, rdf["steps"], world, rdf["ms"]),
+                "unit": "Mcell-updates/s", "ms_per_step": rdf["ms"] / rdf["steps"],
+                "steps": rdf["steps"], "kernel_ms": rdf["kernel_ms"],
+                "note": "the same FP32 step on a double-float state: rho, m, rho E stored as "
+                        "float pairs (+36 B/cell/step), updates and the energy difference in "
+                        "double-float"},
             "configs": configs,
             "gpu_launches": 3 * r32["steps"],
             "clocks": r32["clocks"],

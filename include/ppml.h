@@ -82,9 +82,18 @@ typedef struct {
   int flags;          /* PPML_FIRST_ORDER | PPML_VHAT_1PT variants; 0 = the PPML scheme */
 } ppml_grid_desc;
 
-/* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions). */
+/* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions), and for FP32
+ * states optionally the low parts of the first five.  lo all NULL: a plain float state.
+ * lo all set (FP32 only): a double-float state, field f = f[f] + lo[f] with |lo| at most
+ * half an ulp of f[f], about 48 significant bits.  The stencil arithmetic reads the high
+ * parts; every update of rho, m and rho E is added in double-float and the energy
+ * consistency of Sec. 1.4 takes rho E - |m|^2 / (2 rho) from both parts, so the internal
+ * energy of cold, fast flow (a small difference of large totals) keeps FP64-class
+ * accuracy.  Mixing NULL and non-NULL lo pointers, or lo with PPML_F64, is PPML_E_INVAL;
+ * a step's input and output states carry low parts both or neither. */
 typedef struct {
   void* f[6];
+  void* lo[5];
 } ppml_state;
 
 /* Host copy of the device-resident diagnostics after the last step or dt call. */
@@ -102,9 +111,10 @@ typedef struct {
 typedef struct ppml_grid ppml_grid;
 
 /* Create a handle for the grid in *d and allocate its scratch (U*: five fields of the
- * state's type; reduction partials).  Reads u0 once on `stream` to fix the mean initial
- * density (the vacuum threshold reference, Sec. 1.4) and the first CFL step; synchronizes
- * the stream.  u0 is not modified.  On error *out is NULL. */
+ * state's type, in FP32 also the four low parts of U*'s m and rho E; reduction partials).
+ * Reads u0 once on `stream` to fix the mean initial density (the vacuum threshold
+ * reference, Sec. 1.4) and the first CFL step; synchronizes the stream.  u0 is not
+ * modified.  On error *out is NULL. */
 int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, void* stream, ppml_grid** out);
 
 /* Free the handle and its scratch (synchronizes the device first).  NULL is a no-op. */
@@ -180,8 +190,9 @@ int ppml_fourier_amplitudes(ppml_grid* g, const void* rho, double r_f, int m_max
 int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, double G, unsigned flags,
                           void* stream);
 
-/* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated) into
- * u_star.  For stage-level checks; same dt convention as ppml_step; does not advance t. */
+/* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated; with
+ * their low parts for double-float states) into u_star.  For stage-level checks; same dt
+ * convention as ppml_step; does not advance t. */
 int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star, double dt,
                         void* stream);
 
@@ -215,12 +226,15 @@ int ppml_kernel_times(ppml_grid* g, double ms[3], long long* steps);
  * PPML_NOALLOC_MAX_CELLS cells (about 12 MB, held on every GPU that loads the library
  * until the process exits).  Nothing is allocated by the call (no cudaMalloc/cudaFree).
  *   d         the problem statement (as for ppml_init_grid); nx*ny*nz above the limit
- *             returns PPML_E_INVAL
- *   u_in      input state, not modified; u_out output state (no aliasing)
+ *             returns PPML_E_INVAL; d->t_end must be 0 (the call keeps no simulated time,
+ *             so there is nothing to clip the step against)
+ *   u_in      input state, not modified; u_out output state (no aliasing); plain float
+ *             or double states only (low parts are PPML_E_INVAL here)
  *   dt        step size, > 0 (there is no device-resident step here)
  *   rho_mean  mean initial density, > 0 (reference of the vacuum threshold)
  *   out       NULL, or nine doubles receiving the CFL step of u_out, max|v|, max c and the
- *             six FP64 sums of u_out; non-NULL synchronizes the stream
+ *             six FP64 sums of u_out; non-NULL synchronizes the stream, and only then are
+ *             non-physical output cells reported (PPML_E_NONPHYSICAL, out still filled)
  * The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
  * and sets the kernels' shared-memory limits; make it before any stream capture.  Every
  * call shares the one buffer, which keeps the last call's contents: calls that overlap on
@@ -233,26 +247,38 @@ int ppml_step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in, ppml_stat
  * Many independent 1D problems of uneven lengths (outflow boundaries, gamma shared),
  * advanced by one persistent launch per call.  Each instance keeps its own time, CFL
  * step and end time.  Packed layout: four device arrays (rho, m, rho E, rho eps) of
- * sum(ncells) elements of the batch's type, instance i at [offset_i, offset_i + n_i). */
+ * sum(ncells) elements of the batch's type, instance i at [offset_i, offset_i + n_i).
+ * An FP32 batch stepped with low-part arrays holds rho, m and rho E as double-float pairs
+ * (the stencils read the high parts; updates and the Sec. 1.4 difference use both; the
+ * low parts live in three more caller arrays between calls).  An instance
+ * whose state has a cell with rho <= 0, rho eps <= 0 or a non-finite value stops there
+ * (no further step) and is flagged PPML_FLAG_NONPHYSICAL. */
 typedef struct ppml_batch ppml_batch;
 
 /* ncells[n_inst] (each >= 4), h[n_inst] (> 0), t_end[n_inst] (> 0) are host arrays;
  * they are copied.  vacuum_frac <= 0 selects 1e-5 (reference: each instance's own mean
  * initial density, computed at the first ppml_batch_step).  Every instance must fit in
  * one CTA's shared memory: a one-CTA instance of n cells needs 4 (n + 6) + 4 (n + 1) floats
- * in FP32, 4 (n + 6) + 2 (n + 1) doubles in FP64, plus 1 KB, within the device's opt-in
- * limit (on GB300 up to 7228 FP32 or 4817 FP64 cells); a paired instance (see
- * ppml_batch_set_split) needs the same for m = ceil(n / 2) with 4 (m + 12) + 4 (m + 8)
- * floats or 4 (m + 12) + 2 (m + 8) doubles; else PPML_E_INVAL. */
+ * in FP32 (7 (n + 6) + 4 (n + 1) with low parts), 4 (n + 6) + 2 (n + 1) doubles in FP64,
+ * plus 1 KB, within the device's opt-in limit (on GB300 up to 7228 FP32, 5255 FP32 with
+ * low parts, or 4817 FP64 cells); a paired instance (see ppml_batch_set_split) needs the
+ * same for m = ceil(n / 2) with 4 (m + 12) + 4 (m + 8) floats (7 (m + 12) + 4 (m + 8) with
+ * low parts) or 4 (m + 12) + 2 (m + 8) doubles; else PPML_E_INVAL (for the low parts, at
+ * the ppml_batch_step that passes them). */
 int ppml_batch_init(int n_inst, const int* ncells, const double* h, const double* t_end,
                     double gamma, double cfl, double vacuum_frac, int dtype, ppml_batch** out);
 
 /* Advance every unfinished instance by up to max_steps steps (each instance stops at its
  * t_end) in one launch.  state: four device pointers (see layout), updated in place.
- * If done_host is non-NULL the stream is synchronized and the number of finished
- * instances written there. */
-int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* done_host,
-                    void* stream);
+ * lo: NULL (plain float or double state), or (FP32 only) three device arrays of the state's
+ * layout with the low parts of rho, m, rho E: a double-float state, read at the start and
+ * written at the end of the call (zero them, or set them to x - (float)x of an FP64 x,
+ * before the first call).  If done_host is non-NULL the stream is synchronized, the
+ * number of instances that reached their t_end is written there, and PPML_E_NONPHYSICAL is
+ * returned if some instance stopped on a non-physical state (ppml_batch_status names them);
+ * with done_host NULL the call is asynchronous and reports nothing about the states. */
+int ppml_batch_step(ppml_batch* b, void* const state[4], void* const lo[3], int max_steps,
+                    int* done_host, void* stream);
 
 /* Launch shape of the batch (the paper has no counterpart: a systems choice).  Each
  * instance is one CTA of 256, 512 or 1024 threads; ppml_batch_init selects 512.
@@ -274,9 +300,11 @@ int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_steps, int* t
  * instance or two whole instances of neighbouring sizes (one per CTA), largest first.
  * min_cells = 0: no split (one CTA per instance).  ppml_batch_init selects
  * max(1024, ceil(7 largest / 8)).  Results do not depend on the split (the same operations
- * per cell, in the same order); the work plan is rebuilt (host to device copy).
- * PPML_E_INVAL for 0 < min_cells < 64 or if an instance would not fit (the previous
- * split is kept). */
+ * per cell, in the same order).  The new work plan goes to new device buffers (host to
+ * device copy) and applies to later ppml_batch_step calls; launches already queued and
+ * CUDA graphs captured before keep the plan they were launched with (its buffers live until
+ * ppml_batch_free).  PPML_E_INVAL for 0 < min_cells < 64 or if an instance would not fit
+ * (the previous split is kept). */
 int ppml_batch_set_split(ppml_batch* b, int min_cells);
 
 /* The work plan of a batch of n_inst instances of ncells[i] cells for a split threshold
@@ -290,8 +318,11 @@ int ppml_batch_set_split(ppml_batch* b, int min_cells);
 int ppml_batch_plan(int n_inst, const int* ncells, int split_min, int* items, int* n_items,
                     int* order);
 
-/* Per-instance time reached and steps taken (host arrays of n_inst).  Synchronizes. */
-int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream);
+/* Per-instance time reached, steps taken and flags (PPML_FLAG_NONPHYSICAL for an instance
+ * stopped on a non-physical state); host arrays of n_inst, each may be NULL.  Synchronizes.
+ * Returns PPML_E_NONPHYSICAL (arrays still filled) if some instance is flagged. */
+int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, unsigned* flags_host,
+                      void* stream);
 
 int ppml_batch_free(ppml_batch* b);
 

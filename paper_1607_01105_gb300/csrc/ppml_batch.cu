@@ -24,29 +24,38 @@ struct ppml_batch {
   InstDev* inst;
   int* order;   // one-CTA launch: the instances, largest first
   int2* items;  // cluster launch: the work items, largest first
+  // plans replaced by ppml_batch_set_split: kept until ppml_batch_free, so that launches in
+  // flight and captured graphs keep reading the plan they were launched with
+  std::vector<void*> retired;
   int threads;  // CTA size of the launch: 256, 512 or 1024 (ppml_batch_tune / _set_threads)
   int split_min;         // instances of at least this many cells are split over a CTA pair
   int n_items, n_split;  // cluster launch: items, of which split instances (0: one-CTA launch)
   int nlmax, nmax;       // largest half of a split instance; largest one-CTA instance
-  size_t smem;
+  size_t smem;           // shared memory of a launch; smem_df with low parts (FP32)
+  size_t smem_df;
+  int max_smem;          // the device's opt-in limit per CTA
 };
 
 namespace {
 constexpr int kBatchSizes[3] = {256, 512, 1024};
 constexpr int kSplitFloor = 64;  // smallest instance a CTA pair may take
 
-// Shared memory of one CTA: four fields padded by `pad` on each side and `nface` face
-// arrays of `faces` values.
-size_t batch_smem(int cells, int pad, int nface, int faces, size_t elt) {
-  return (4 * (size_t)(cells + 2 * pad) + (size_t)nface * faces) * elt;
+// Shared memory of one CTA: four fields (and for a double-float batch the three low parts)
+// padded by `pad` on each side and `nface` face arrays of `faces` values.
+size_t batch_smem(int cells, int pad, int nface, int nlo, int faces, size_t elt) {
+  return ((4 + (size_t)nlo) * (size_t)(cells + 2 * pad) + (size_t)nface * faces) * elt;
 }
 
 // Work plan for b->split_min (ppml_batch_plan): with no instance split, one CTA per
 // instance (largest first); else one cluster of two CTAs per work item, ordered largest
-// first.  Sizes the launch's shared memory and copies the plan to the device.
+// first.  Sizes the launch's shared memory and copies the plan to new device buffers; the
+// previous plan's buffers are retired (kept until the handle is freed), so a launch in
+// flight or a captured graph never sees a half-written plan or a plan that does not match
+// its shared-memory size.
 int plan_batch(ppml_batch* b) {
   const size_t elt = b->dtype == PPML_F64 ? 8 : 4;
   const int nface = b->dtype == PPML_F64 ? kBatchFaceArrays<double> : kBatchFaceArrays<float>;
+  const int nlo = b->dtype == PPML_F64 ? 0 : kBatchLoArrays;
   std::vector<int> items(2 * (size_t)b->n_inst), order(b->n_inst);
   int n_items = 0;
   int rc = ppml_batch_plan(b->n_inst, b->ncells.data(), b->split_min, items.data(), &n_items,
@@ -61,9 +70,12 @@ int plan_batch(ppml_batch* b) {
       nmax = std::max(nmax, b->ncells[i]);
     }
   }
-  const size_t smem_split = n_split ? batch_smem(nlmax, kPairHalo, nface, nlmax + 8, elt) : 0;
-  const size_t smem_one = nmax ? batch_smem(nmax, kBatchGhost, nface, nmax + 1, elt) : 0;
-  const size_t smem = std::max(smem_split, smem_one);
+  auto smem_for = [&](int lo_arrays) {
+    const size_t a = n_split ? batch_smem(nlmax, kPairHalo, nface, lo_arrays, nlmax + 8, elt) : 0;
+    const size_t c = nmax ? batch_smem(nmax, kBatchGhost, nface, lo_arrays, nmax + 1, elt) : 0;
+    return std::max(a, c);
+  };
+  const size_t smem = smem_for(0), smem_df = smem_for(nlo);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -72,54 +84,104 @@ int plan_batch(ppml_batch* b) {
                      "largest instance needs %zu bytes of shared memory (> %d): %d cells on one "
                      "CTA, %d cells per CTA of a split one",
                      smem, maxsm, nmax, nlmax);
-  if (n_items > 0) {
-    if (cudaMemcpy(b->items, items.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-      return ppml_fail(PPML_E_CUDA, "batch items copy: %s", cudaGetErrorString(cudaGetLastError()));
-  } else if (cudaMemcpy(b->order, order.data(), sizeof(int) * b->n_inst,
-                        cudaMemcpyHostToDevice) != cudaSuccess) {
-    return ppml_fail(PPML_E_CUDA, "batch order copy: %s", cudaGetErrorString(cudaGetLastError()));
+  int* d_order = nullptr;
+  int2* d_items = nullptr;
+  if (cudaMalloc(&d_order, sizeof(int) * b->n_inst) != cudaSuccess ||
+      cudaMalloc(&d_items, sizeof(int2) * b->n_inst) != cudaSuccess) {
+    if (d_order) cudaFree(d_order);
+    return ppml_fail(PPML_E_NOMEM, "cudaMalloc of the batch work plan failed");
   }
+  const cudaError_t e =
+      n_items > 0
+          ? cudaMemcpy(d_items, items.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice)
+          : cudaMemcpy(d_order, order.data(), sizeof(int) * b->n_inst, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d_order);
+    cudaFree(d_items);
+    return ppml_fail(PPML_E_CUDA, "batch plan copy: %s", cudaGetErrorString(e));
+  }
+  if (b->order) b->retired.push_back(b->order);
+  if (b->items) b->retired.push_back(b->items);
+  b->order = d_order;
+  b->items = d_items;
   b->n_items = n_items;
   b->n_split = n_split;
   b->nlmax = nlmax;
   b->nmax = nmax;
   b->smem = smem;
+  b->smem_df = smem_df;
+  b->max_smem = maxsm;
   return PPML_OK;
 }
 
 template <typename T>
-int launch_typed_t(ppml_batch* b, void* const state[4], InstDev* inst, int max_steps,
-                   int threads, cudaStream_t st) {
+int launch_typed_t(ppml_batch* b, void* const state[4], void* const lo[3], InstDev* inst,
+                   int max_steps, int threads, cudaStream_t st) {
   T* f[4] = {(T*)state[0], (T*)state[1], (T*)state[2], (T*)state[3]};
+  BatchLo<T> L;
+  for (int q = 0; q < 3; q++) L.p[q] = lo ? (T*)lo[q] : nullptr;
+  const size_t smem = lo ? b->smem_df : b->smem;
+  if (smem + 1024 > (size_t)b->max_smem)
+    return ppml_fail(PPML_E_INVAL,
+                     "with low parts the largest instance needs %zu bytes of shared memory (> %d)",
+                     smem, b->max_smem);
   int rc = launch_batch_vacuum<T>(f[0], inst, b->n_inst, st);
   if (rc) return rc;
   if (b->n_items == 0)
-    return launch_batch<T>(f[0], f[1], f[2], f[3], inst, b->order, b->gamma, b->cfl, max_steps,
-                           b->nmax, b->n_inst, b->smem, threads, st);
-  return launch_batch_cluster<T>(f[0], f[1], f[2], f[3], inst, b->items, b->gamma, b->cfl,
-                                 max_steps, b->nlmax, b->nmax, b->n_items, b->smem, threads, st);
+    return launch_batch<T>(f[0], f[1], f[2], f[3], L, inst, b->order, b->gamma, b->cfl, max_steps,
+                           b->nmax, b->n_inst, smem, threads, st);
+  return launch_batch_cluster<T>(f[0], f[1], f[2], f[3], L, inst, b->items, b->gamma, b->cfl,
+                                 max_steps, b->nlmax, b->nmax, b->n_items, smem, threads, st);
 }
 
 void release_batch(ppml_batch* b) {
   if (b->inst) cudaFree(b->inst);
   if (b->order) cudaFree(b->order);
   if (b->items) cudaFree(b->items);
+  for (void* p : b->retired) cudaFree(p);
   delete b;
 }
 
-int launch_typed(ppml_batch* b, void* const state[4], InstDev* inst, int max_steps, int threads,
-                 cudaStream_t st) {
-  return b->dtype == PPML_F64 ? launch_typed_t<double>(b, state, inst, max_steps, threads, st)
-                              : launch_typed_t<float>(b, state, inst, max_steps, threads, st);
+int launch_typed(ppml_batch* b, void* const state[4], void* const lo[3], InstDev* inst,
+                 int max_steps, int threads, cudaStream_t st) {
+  return b->dtype == PPML_F64
+             ? launch_typed_t<double>(b, state, lo, inst, max_steps, threads, st)
+             : launch_typed_t<float>(b, state, lo, inst, max_steps, threads, st);
 }
 
-int check_state(void* const state[4]) {
+int check_state(const ppml_batch* b, void* const state[4], void* const lo[3]) {
   if (!state) return ppml_fail(PPML_E_INVAL, "state is NULL");
   for (int f = 0; f < 4; f++) {
     if (!state[f]) return ppml_fail(PPML_E_INVAL, "state field %d is NULL", f);
     if (((uintptr_t)state[f]) & 15u) return ppml_fail(PPML_E_INVAL, "state field %d misaligned", f);
   }
+  if (lo) {
+    if (b->dtype != PPML_F32) return ppml_fail(PPML_E_INVAL, "low parts are for FP32 batches only");
+    for (int f = 0; f < 3; f++) {
+      if (!lo[f]) return ppml_fail(PPML_E_INVAL, "low part %d is NULL (pass lo = NULL for none)", f);
+      if (((uintptr_t)lo[f]) & 15u) return ppml_fail(PPML_E_INVAL, "low part %d misaligned", f);
+      for (int q = 0; q < 4; q++)
+        if (lo[f] == state[q]) return ppml_fail(PPML_E_INVAL, "low part %d aliases a field", f);
+    }
+  }
+  return PPML_OK;
+}
+
+// Copy the instances' metadata to the host; counts the stopped and the flagged ones.
+int read_instances(const ppml_batch* b, std::vector<InstDev>& hi, int* n_done, int* n_bad,
+                   cudaStream_t st) {
+  hi.resize(b->n_inst);
+  if (cudaMemcpyAsync(hi.data(), b->inst, sizeof(InstDev) * b->n_inst, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ppml_fail(PPML_E_CUDA, "batch status: %s", cudaGetErrorString(cudaGetLastError()));
+  int d = 0, nb = 0;
+  for (auto& x : hi) {
+    d += x.done && !x.bad;
+    nb += x.bad;
+  }
+  if (n_done) *n_done = d;
+  if (n_bad) *n_bad = nb;
   return PPML_OK;
 }
 }  // namespace
@@ -187,7 +249,7 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
     hi[i].t = 0.0;
     hi[i].rho_vac = -vacuum_frac;  // fixed at the first step from the mean density
     hi[i].done = 0;
-    hi[i].pad = 0;
+    hi[i].bad = 0;
     off += ncells[i];
     nmax = std::max(nmax, ncells[i]);
   }
@@ -205,9 +267,7 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
   // costs more than the halved work saves
   b->split_min = std::max(1024, (7 * nmax + 7) / 8);
   int rc = PPML_OK;
-  if (cudaMalloc(&b->inst, sizeof(InstDev) * n_inst) != cudaSuccess ||
-      cudaMalloc(&b->order, sizeof(int) * n_inst) != cudaSuccess ||
-      cudaMalloc(&b->items, sizeof(int2) * n_inst) != cudaSuccess)
+  if (cudaMalloc(&b->inst, sizeof(InstDev) * n_inst) != cudaSuccess)
     rc = ppml_fail(PPML_E_NOMEM, "cudaMalloc of batch metadata failed");
   else if (cudaMemcpy(b->inst, hi.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice) !=
            cudaSuccess)
@@ -223,25 +283,24 @@ extern "C" int ppml_batch_init(int n_inst, const int* ncells, const double* h,
   return PPML_OK;
 }
 
-extern "C" int ppml_batch_step(ppml_batch* b, void* const state[4], int max_steps, int* done_host,
-                               void* stream) {
+extern "C" int ppml_batch_step(ppml_batch* b, void* const state[4], void* const lo[3],
+                               int max_steps, int* done_host, void* stream) {
   ppml_clear_error();
   if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
-  int rc = check_state(state);
+  int rc = check_state(b, state, lo);
   if (rc) return rc;
   if (max_steps < 0) return ppml_fail(PPML_E_INVAL, "max_steps < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  rc = launch_typed(b, state, b->inst, max_steps, b->threads, st);
+  rc = launch_typed(b, state, lo, b->inst, max_steps, b->threads, st);
   if (rc) return rc;
   if (done_host) {
-    std::vector<InstDev> hi(b->n_inst);
-    if (cudaMemcpyAsync(hi.data(), b->inst, sizeof(InstDev) * b->n_inst, cudaMemcpyDeviceToHost,
-                        st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return ppml_fail(PPML_E_CUDA, "batch status: %s", cudaGetErrorString(cudaGetLastError()));
-    int d = 0;
-    for (auto& x : hi) d += x.done;
-    *done_host = d;
+    std::vector<InstDev> hi;
+    int n_bad = 0;
+    rc = read_instances(b, hi, done_host, &n_bad, st);
+    if (rc) return rc;
+    if (n_bad)
+      return ppml_fail(PPML_E_NONPHYSICAL, "%d instance(s) stopped on a non-physical state "
+                                           "(ppml_batch_status names them)", n_bad);
   }
   return PPML_OK;
 }
@@ -264,11 +323,8 @@ extern "C" int ppml_batch_set_split(ppml_batch* b, int min_cells) {
     return ppml_fail(PPML_E_INVAL, "min_cells = %d: 0 (no pairs) or >= %d", min_cells, kSplitFloor);
   const int old = b->split_min;
   b->split_min = min_cells;
-  const int rc = plan_batch(b);
-  if (rc) {
-    b->split_min = old;
-    plan_batch(b);
-  }
+  const int rc = plan_batch(b);  // the current plan stays in place if this fails
+  if (rc) b->split_min = old;
   return rc;
 }
 
@@ -276,7 +332,7 @@ extern "C" int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_st
                                int* threads_out, double ms_out[3], void* stream) {
   ppml_clear_error();
   if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
-  int rc = check_state(state);
+  int rc = check_state(b, state, nullptr);
   if (rc) return rc;
   if (trial_steps < 1) return ppml_fail(PPML_E_INVAL, "trial_steps = %d must be >= 1", trial_steps);
   cudaStream_t st = (cudaStream_t)stream;
@@ -308,7 +364,7 @@ extern "C" int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_st
         rc = ppml_fail(PPML_E_CUDA, "tuning copy: %s", cudaGetErrorString(cudaGetLastError()));
       if (rc) break;
       cudaEventRecord(e0, st);
-      rc = launch_typed(b, scratch, inst, trial_steps, threads, st);
+      rc = launch_typed(b, scratch, nullptr, inst, trial_steps, threads, st);
       if (rc) break;
       cudaEventRecord(e1, st);
       float ms = 0.f;
@@ -334,19 +390,21 @@ extern "C" int ppml_batch_tune(ppml_batch* b, void* const state[4], int trial_st
   return PPML_OK;
 }
 
-extern "C" int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host, void* stream) {
+extern "C" int ppml_batch_status(ppml_batch* b, double* t_host, int* steps_host,
+                                 unsigned* flags_host, void* stream) {
   ppml_clear_error();
   if (!b) return ppml_fail(PPML_E_INVAL, "batch is NULL");
-  std::vector<InstDev> hi(b->n_inst);
-  cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(hi.data(), b->inst, sizeof(InstDev) * b->n_inst, cudaMemcpyDeviceToHost, st) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return ppml_fail(PPML_E_CUDA, "batch status: %s", cudaGetErrorString(cudaGetLastError()));
+  std::vector<InstDev> hi;
+  int n_bad = 0;
+  int rc = read_instances(b, hi, nullptr, &n_bad, (cudaStream_t)stream);
+  if (rc) return rc;
   for (int i = 0; i < b->n_inst; i++) {
     if (t_host) t_host[i] = hi[i].t;
     if (steps_host) steps_host[i] = hi[i].steps;
+    if (flags_host) flags_host[i] = hi[i].bad ? PPML_FLAG_NONPHYSICAL : 0u;
   }
+  if (n_bad)
+    return ppml_fail(PPML_E_NONPHYSICAL, "%d instance(s) stopped on a non-physical state", n_bad);
   return PPML_OK;
 }
 

@@ -1,7 +1,11 @@
 // Batched independent 1D problems (many shock tubes of uneven lengths) advanced by one
 // persistent launch: each instance keeps its four fields (rho, m, rho E, rho eps) resident
 // in shared memory for all of its steps, takes its own CFL step (Sec. 1.1) and stops at its
-// own end time.  An instance is owned by one CTA, or -- the longest ones -- split over the
+// own end time, or at the first step whose state has a cell with rho <= 0, rho eps <= 0 or
+// a non-finite value (the instance is then flagged non-physical).  An FP32 batch given
+// low-part arrays keeps rho, m and rho E as double-float pairs (the high parts feed the
+// stencils, every update is added to the pair, and the Sec. 1.4 difference
+// rho E - m^2 / (2 rho) is formed from both parts): FP64-class storage of the totals.  An instance is owned by one CTA, or -- the longest ones -- split over the
 // two CTAs of a cluster, which exchange a halo and their CFL maxima once per step; no
 // other CTAs wait on one another.  The scheme per step is the 1D case of Sec. 1: Eulerian
 // face solve, upwind Lagrangian fluxes, energy correction of Sec. 1.4.  In 1D the 9-point
@@ -22,10 +26,15 @@ constexpr int kBatchGhost = 3;
 // FP64 takes the fields in turn through two, so that 4096-cell instances fit in 227 KB.
 template <typename T>
 constexpr int kBatchFaceArrays = sizeof(T) == 4 ? 4 : 2;
+// A double-float FP32 batch keeps three more arrays of the instance's cells: the low parts
+// of rho, m, rho E.
+constexpr int kBatchLoArrays = 3;
 // An instance split over a CTA pair: halo cells facing the partner, and the exchange slot
-// (the kPairHalo edge cells of the four fields, then the two CFL maxima).
+// (the kPairHalo edge cells of the four fields and, double-float, of the low parts, then
+// the two CFL maxima and the non-physical flag).
 constexpr int kPairHalo = 6;
-constexpr int kPairSlot = 4 * kPairHalo + 2;
+constexpr int kPairFieldsMax = 4 + kBatchLoArrays;
+constexpr int kPairSlot = kPairFieldsMax * kPairHalo + 3;
 
 __device__ __forceinline__ unsigned cluster_rank() {
   return cooperative_groups::this_cluster().block_rank();
@@ -38,7 +47,8 @@ struct InstDev {
   int n;          // cells
   int steps;      // steps taken so far
   double h, t_end, t, rho_vac;
-  int done, pad;
+  int done;  // stopped: t_end reached, the step underflowed, or non-physical
+  int bad;   // a state of the instance had rho <= 0, rho eps <= 0 or a non-finite value
 };
 
 template <typename T>
@@ -182,17 +192,20 @@ __device__ __forceinline__ T vel_of(T m, T r) {
 
 // Thread 0's CFL decision from the instance's maxima A = max|v|, B = max c (Sec. 1.1).
 // Thread 0 alone keeps the instance's time (t, steps, done): it stops once t has reached
-// t_end, else forms tau clipped to the remaining time and advances t.  FP64 forms tau =
+// t_end or when the current state is non-physical (bad: flagged, no step taken), else forms
+// tau clipped to the remaining time and advances t.  FP64 forms tau =
 // cfl h / (A + B) and tau / h as the checker does; FP32 forms tau / h = cfl / (A + B) in
 // FP32 and tau = (tau / h) h in FP64 (both divisions of the FP64 form, at the FP64 pipe's
 // latency, would lie on every step's critical path).  Publishes tau (sh[64]), tau / h
 // (sh + 66) and the go flag (sh + 68).
 template <typename T>
-__device__ __forceinline__ void cfl_decide(T A, T B, double cfl, InstDev& I, double* sh) {
+__device__ __forceinline__ void cfl_decide(T A, T B, bool bad, double cfl, InstDev& I,
+                                           double* sh) {
   int go = 0;
   double d = 0.0;
   T q = T(0);
-  if (!(I.t >= I.t_end)) {
+  if (bad) I.bad = 1;
+  if (!bad && !(I.t >= I.t_end)) {
     const double rem = I.t_end - I.t;
     if constexpr (sizeof(T) == 4) {
       q = (float)cfl / (A + B);
@@ -250,20 +263,21 @@ __device__ __forceinline__ void fold_maxima(const double* sh, T& A, T& B) {
 }
 
 // CFL step of the CTA's instance (Sec. 1.1) from the per-thread maxima a = max|v|,
-// b = max c: warp maxima, then warp 0 folds the warps' (maxima in the state's precision;
-// a maximum is exact in any) and thread 0 decides (cfl_decide).  Returns whether the CTA
-// takes the step (the same in every thread), with th = tau / h and dt = tau.  Two
-// barriers; the caller puts at least one more between two calls, so the next call's
-// writes to sh cannot overtake this call's reads.
+// b = max c and non-physical flags: warp maxima, then warp 0 folds the warps' (maxima in
+// the state's precision; a maximum is exact in any), the flags are OR-ed by the barrier,
+// and thread 0 decides (cfl_decide).  Returns whether the CTA takes the step (the same in
+// every thread), with th = tau / h and dt = tau.  Two barriers; the caller puts at least
+// one more between two calls, so the next call's writes to sh cannot overtake this
+// call's reads.
 template <typename T>
-__device__ __forceinline__ bool block_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
-                                               double& dt, T& th) {
+__device__ __forceinline__ bool block_cfl_step(T a, T b, bool bad, double cfl, InstDev& I,
+                                               double* sh, double& dt, T& th) {
   warp_maxima<T>(a, b, sh);
-  __syncthreads();
+  const bool any_bad = __syncthreads_or(bad) != 0;
   if (threadIdx.x < 32) {
     T A, B;
     fold_maxima<T>(sh, A, B);
-    if (threadIdx.x == 0) cfl_decide<T>(A, B, cfl, I, sh);
+    if (threadIdx.x == 0) cfl_decide<T>(A, B, any_bad, cfl, I, sh);
   }
   __syncthreads();
   dt = sh[64];
@@ -306,45 +320,49 @@ struct Part {
 };
 
 // CFL step of an instance split over a CTA pair (Sec. 1.1), with the halo exchange.  Each
-// CTA reduces its maxima and publishes them, with its kPairHalo edge cells of the four
-// fields next to the partner, in slot `par` of its shared memory; after the cluster
-// barrier it copies the partner's edge cells into its halo through distributed shared
-// memory, and thread 0 decides from the larger of the two CTAs' maxima (cfl_decide).  Both
-// thread 0s hold the same time and see the same maxima, so both CTAs take the same
-// decisions and meet the same barriers.  The slots alternate with the step's parity: a
-// slot is rewritten two steps later, after the next cluster barrier, which the partner
-// passes only after its reads of this one.  Fields R, M, E, Ei are padded by kPairHalo.
-template <typename T>
-__device__ __forceinline__ bool pair_cfl_step(T a, T b, double cfl, InstDev& I, double* sh,
-                                              T* xslot, int par, const Part& P, T* R, T* M,
-                                              T* E, T* Ei, double& dt, T& th) {
+// CTA reduces its maxima and non-physical flags and publishes them, with its kPairHalo
+// edge cells next to the partner of the four fields and (FP32) of the three low parts, in
+// slot `par` of its shared memory; after the cluster barrier it copies the partner's edge
+// cells into its halo through distributed shared memory, and thread 0 decides from the
+// larger of the two CTAs' maxima and either flag (cfl_decide).  Both thread 0s hold the
+// same time and see the same maxima and flags, so both CTAs take the same decisions and
+// meet the same barriers.  The slots alternate with the step's parity: a slot is
+// rewritten two steps later, after the next cluster barrier, which the partner passes
+// only after its reads of this one.  q[0..NF) are the padded arrays (R, M, E, Ei, then
+// RL, ML, EL for a double-float batch), padded by kPairHalo.
+template <typename T, int NF>
+__device__ __forceinline__ bool pair_cfl_step(T a, T b, bool bad, double cfl, InstDev& I,
+                                              double* sh, T* xslot, int par, const Part& P,
+                                              T* const* q, double& dt, T& th) {
   constexpr int G = kPairHalo;
+  constexpr int SL = kPairSlot;
   warp_maxima<T>(a, b, sh);
-  __syncthreads();  // orders the step's last stores and the warp maxima
-  T* slot = xslot + par * kPairSlot;
+  const bool any_bad = __syncthreads_or(bad) != 0;  // orders the step's last stores too
+  T* slot = xslot + par * SL;
+  if (threadIdx.x < NF * kPairHalo) {  // rank 0 publishes cells nl-6 .. nl-1, rank 1 0 .. 5
+    const int f = threadIdx.x / kPairHalo, k = threadIdx.x % kPairHalo;
+    slot[threadIdx.x] = q[f][G + (P.gl ? P.nl - kPairHalo : 0) + k];
+  }
   if (threadIdx.x < 32) {
-    if (threadIdx.x < 4 * kPairHalo) {  // rank 0 publishes cells nl-6 .. nl-1, rank 1 0 .. 5
-      const int f = threadIdx.x / kPairHalo, k = threadIdx.x % kPairHalo;
-      const T* q = f == 0 ? R : f == 1 ? M : f == 2 ? E : Ei;
-      slot[threadIdx.x] = q[G + (P.gl ? P.nl - kPairHalo : 0) + k];
-    }
     T A, B;
     fold_maxima<T>(sh, A, B);
     if (threadIdx.x == 0) {
-      slot[4 * kPairHalo] = A;
-      slot[4 * kPairHalo + 1] = B;
+      slot[NF * kPairHalo] = A;
+      slot[NF * kPairHalo + 1] = B;
+      slot[NF * kPairHalo + 2] = any_bad ? T(1) : T(0);
     }
   }
   cluster_sync();
   const T* rslot = cooperative_groups::this_cluster().map_shared_rank(slot, cluster_rank() ^ 1u);
-  if (threadIdx.x < 4 * kPairHalo) {  // rank 0's halo is cells nl .. nl+5, rank 1's -6 .. -1
+  if (threadIdx.x < NF * kPairHalo) {  // rank 0's halo is cells nl .. nl+5, rank 1's -6 .. -1
     const int f = threadIdx.x / kPairHalo, k = threadIdx.x % kPairHalo;
-    T* q = f == 0 ? R : f == 1 ? M : f == 2 ? E : Ei;
-    q[G + (P.gl ? P.nl : -kPairHalo) + k] = rslot[threadIdx.x];
+    q[f][G + (P.gl ? P.nl : -kPairHalo) + k] = rslot[threadIdx.x];
   }
   if (threadIdx.x == 0)
-    cfl_decide<T>(fmax(slot[4 * kPairHalo], rslot[4 * kPairHalo]),
-                  fmax(slot[4 * kPairHalo + 1], rslot[4 * kPairHalo + 1]), cfl, I, sh);
+    cfl_decide<T>(fmax(slot[NF * kPairHalo], rslot[NF * kPairHalo]),
+                  fmax(slot[NF * kPairHalo + 1], rslot[NF * kPairHalo + 1]),
+                  slot[NF * kPairHalo + 2] != T(0) || rslot[NF * kPairHalo + 2] != T(0), cfl, I,
+                  sh);
   __syncthreads();
   dt = sh[64];
   th = *reinterpret_cast<const T*>(sh + 66);
@@ -355,15 +373,18 @@ __device__ __forceinline__ bool pair_cfl_step(T a, T b, double cfl, InstDev& I, 
 // the part is half of an instance and the partner CTA of the cluster holds the other half
 // (halo exchange and common CFL step in pair_cfl_step); else the part is the instance.
 // Local arrays: four fields with G cells of padding on each side (the halo facing the
-// partner, outflow ghosts at the instance's ends), face arrays indexed f + FO.
-template <typename T, int NTHREADS, bool PAIR>
+// partner, outflow ghosts at the instance's ends), face arrays indexed f + FO, and (DF,
+// FP32 only) the low parts of rho, m, rho E padded like the fields, read from g_lo at the
+// start and written back at the end.
+template <typename T, int NTHREADS, bool PAIR, bool DF>
 __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restrict__ g_m,
                                              T* __restrict__ g_en, T* __restrict__ g_ei,
-                                             InstDev& I, const Part P, T* smem, int stride,
-                                             int nface, double gamma_d, double cfl,
+                                             T* const* g_lo, InstDev& I, const Part P, T* smem,
+                                             int stride, int nface, double gamma_d, double cfl,
                                              int max_steps, double* red, T* xslot) {
   constexpr int G = PAIR ? kPairHalo : kBatchGhost;
   constexpr int FO = PAIR ? 3 : 0;
+  static_assert(!DF || sizeof(T) == 4, "double-float states are FP32 only");
   const int nl = P.nl;
   T* R = smem;
   T* M = R + stride;
@@ -373,6 +394,10 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
   T* FB = FA + nface;   // face array B (P, then fluxes)
   T* FC = FB + nface;   // FP32 only: the rho E and rho eps fluxes
   T* FD = FC + nface;
+  T* RL = FA + kBatchFaceArrays<T> * nface;  // DF: low parts of rho, m, rho E
+  T* ML = RL + stride;
+  T* EL = ML + stride;
+  T* const fields[7] = {R, M, E, Ei, RL, ML, EL};
   const int tid = threadIdx.x;
   const T gamma = T(gamma_d), gm1 = T(gamma_d - 1.0);
   // faces per streamed run: one run per thread covers the pass's faces; at least 9 (the
@@ -399,9 +424,14 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
     }
   };
   // CFL maxima (Sec. 1.1) over the cells a thread owns, taken as each cell's final value
-  // of a step is written: max |v| and max c, in the checker's per-cell operations
+  // of a step is written: max |v| and max c, in the checker's per-cell operations; and
+  // whether one of them is non-physical (rho <= 0, rho eps <= 0 or a non-finite field)
   T vm = T(0), cm = T(0);
-  auto cfl_cell = [&](T r, T m, T ei, bool valid) {
+  bool bad = false;
+  auto cfl_cell = [&](T r, T m, T en, T ei, bool valid) {
+    const bool ok = r > T(0) && ei > T(0) && isfinite(r) && isfinite(m) && isfinite(en) &&
+                    isfinite(ei);
+    bad = bad || (valid && !ok);
     const T p = gm1 * ei;
     T v, cs;
     if constexpr (sizeof(T) == 4) {
@@ -424,7 +454,12 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
     M[g] = m;
     E[g] = en;
     Ei[g] = ei;
-    cfl_cell(r, m, ei, true);
+    if constexpr (DF) {
+      RL[g] = g_lo[0][off + c];
+      ML[g] = g_lo[1][off + c];
+      EL[g] = g_lo[2][off + c];
+    }
+    cfl_cell(r, m, en, ei, true);
   }
   outer_ghosts(R, 0);
   outer_ghosts(M, 0);
@@ -438,6 +473,11 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
       M[G + h0 + tid] = g_m[gi];
       E[G + h0 + tid] = g_en[gi];
       Ei[G + h0 + tid] = g_ei[gi];
+      if constexpr (DF) {
+        RL[G + h0 + tid] = g_lo[0][gi];
+        ML[G + h0 + tid] = g_lo[1][gi];
+        EL[G + h0 + tid] = g_lo[2][gi];
+      }
     }
   }
   // Upwind Lagrangian fluxes of one field at the own faces 0 .. nl (Sec. 1.3)
@@ -463,9 +503,10 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
     T th;
     bool go;
     if constexpr (PAIR)
-      go = pair_cfl_step<T>(vm, cm, cfl, I, red, xslot, s & 1, P, R, M, E, Ei, dt, th);
+      go = pair_cfl_step<T, DF ? 7 : 4>(vm, cm, bad, cfl, I, red, xslot, s & 1, P, fields, dt,
+                                        th);
     else
-      go = block_cfl_step<T>(vm, cm, cfl, I, red, dt, th);
+      go = block_cfl_step<T>(vm, cm, bad, cfl, I, red, dt, th);
     if (!go) break;
     // Eulerian stage: faces fa .. fb; each thread streams one run of consecutive faces
     {
@@ -508,7 +549,7 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
     // cells c0 + u NTHREADS, u < kU, per pass: every load of the pass ahead of its stores
     // (the compiler cannot move a load past a store into the same shared array)
     for (int c0 = P.ca + tid; c0 < P.cb; c0 += kU * NTHREADS) {
-      T Vm[kU], Vp[kU], Pm[kU], Pp[kU], m0[kU], e0[kU], ei0[kU];
+      T Vm[kU], Vp[kU], Pm[kU], Pp[kU], m0[kU], e0[kU], ei0[kU], ml0[kU], el0[kU];
 #pragma unroll
       for (int u = 0; u < kU; u++) {
         const int c = min(c0 + u * NTHREADS, P.cb - 1), g = c + G;
@@ -519,16 +560,25 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
         m0[u] = M[g];
         e0[u] = E[g];
         ei0[u] = Ei[g];
+        if constexpr (DF) {
+          ml0[u] = ML[g];
+          el0[u] = EL[g];
+        }
       }
 #pragma unroll
       for (int u = 0; u < kU; u++) {
         const int c = c0 + u * NTHREADS, g = c + G;
         if (c < P.cb) {
-          const T m1 = m0[u] - th * (Pp[u] - Pm[u]);
-          const T e1 = e0[u] - th * (Pp[u] * Vp[u] - Pm[u] * Vm[u]);
+          const T dm = th * (Pp[u] - Pm[u]);
+          const T de = th * (Pp[u] * Vp[u] - Pm[u] * Vm[u]);
           const T ei1 = ei0[u] - gm1 * ei0[u] * (th * (Vp[u] - Vm[u]));
-          M[g] = m1;
-          E[g] = e1;
+          if constexpr (DF) {
+            df_sub(m0[u], ml0[u], dm, M[g], ML[g]);
+            df_sub(e0[u], el0[u], de, E[g], EL[g]);
+          } else {
+            M[g] = m0[u] - dm;
+            E[g] = e0[u] - de;
+          }
           Ei[g] = ei1;
         }
       }
@@ -572,18 +622,29 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
       vm = T(0);
       cm = T(0);
       for (int c0 = tid; c0 < nl; c0 += kU * NTHREADS) {
-        float q[kU][4];
+        // every field's update (DF: rho, m, rho E added to their double-float pairs)
+        float q[kU][4], ql[kU][3];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
           const int c = min(c0 + u * NTHREADS, nl - 1), g = c + G;
-          q[u][0] = R[g] - th * (FA[c + 1 + FO] - FA[c + FO]);
-          q[u][1] = M[g] - th * (FB[c + 1 + FO] - FB[c + FO]);
-          q[u][2] = E[g] - th * (FC[c + 1 + FO] - FC[c + FO]);
+          const float d0 = th * (FA[c + 1 + FO] - FA[c + FO]);
+          const float d1 = th * (FB[c + 1 + FO] - FB[c + FO]);
+          const float d2 = th * (FC[c + 1 + FO] - FC[c + FO]);
+          if constexpr (DF) {
+            df_sub(R[g], RL[g], d0, q[u][0], ql[u][0]);
+            df_sub(M[g], ML[g], d1, q[u][1], ql[u][1]);
+            df_sub(E[g], EL[g], d2, q[u][2], ql[u][2]);
+          } else {
+            q[u][0] = R[g] - d0;
+            q[u][1] = M[g] - d1;
+            q[u][2] = E[g] - d2;
+            ql[u][0] = ql[u][1] = ql[u][2] = 0.0f;
+          }
           q[u][3] = Ei[g] - th * (FD[c + 1 + FO] - FD[c + FO]);
         }
         // Sec. 1.4: the dense branch for all kU cells without control flow (so that
         // their chains interleave), then the rare vacuum cells
-        float w[kU][6];
+        float w[kU][6], wl[kU][5];
         bool vac[kU], any_vac = false;
 #pragma unroll
         for (int u = 0; u < kU; u++) {
@@ -593,16 +654,25 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
           w[u][3] = 0.0f;
           w[u][4] = q[u][2];
           w[u][5] = q[u][3];
+          wl[u][0] = ql[u][0];
+          wl[u][1] = ql[u][1];
+          wl[u][2] = 0.0f;
+          wl[u][3] = 0.0f;
+          wl[u][4] = ql[u][2];
           vac[u] = vacuum_cell_f32(w[u], rho_vac_up);
           any_vac |= vac[u];
-          q[u][3] = dense_eps_f32(w[u]);
+          q[u][3] = DF ? dense_eps_df(w[u], wl[u]) : dense_eps_f32(w[u]);
         }
         if (any_vac) {
 #pragma unroll
           for (int u = 0; u < kU; u++)
             if (vac[u]) {
-              vacuum_correct_f32(w[u], I.rho_vac);
+              if constexpr (DF)
+                vacuum_correct_df(w[u], wl[u], I.rho_vac);
+              else
+                vacuum_correct_f32(w[u], I.rho_vac);
               q[u][1] = w[u][1];
+              ql[u][1] = wl[u][1];
               q[u][3] = w[u][5];
             }
         }
@@ -614,12 +684,18 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
             M[g] = q[u][1];
             E[g] = q[u][2];
             Ei[g] = q[u][3];
+            if constexpr (DF) {
+              RL[g] = ql[u][0];
+              ML[g] = ql[u][1];
+              EL[g] = ql[u][2];
+            }
           }
         }
         // next step's CFL maxima over the valid cells (a clamped duplicate may have read
         // a cell its owner has already updated)
 #pragma unroll
-        for (int u = 0; u < kU; u++) cfl_cell(q[u][0], q[u][1], q[u][3], c0 + u * NTHREADS < nl);
+        for (int u = 0; u < kU; u++)
+          cfl_cell(q[u][0], q[u][1], q[u][2], q[u][3], c0 + u * NTHREADS < nl);
       }
     } else {
       // FP64 Lagrangian stage: v hat at faces, then each field's flux and update in turn
@@ -652,7 +728,7 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
         correct_energy<T>(u, I.rho_vac);
         M[g] = u[1];
         Ei[g] = u[5];
-        cfl_cell(r, u[1], u[5], true);
+        cfl_cell(r, u[1], en, u[5], true);
       }
     }
     outer_ghosts(R, 0);
@@ -666,14 +742,25 @@ __device__ __forceinline__ void advance_part(T* __restrict__ g_rho, T* __restric
     g_m[off + c] = M[c + G];
     g_en[off + c] = E[c + G];
     g_ei[off + c] = Ei[c + G];
+    if constexpr (DF) {
+      g_lo[0][off + c] = RL[c + G];
+      g_lo[1][off + c] = ML[c + G];
+      g_lo[2][off + c] = EL[c + G];
+    }
   }
 }
 
-template <typename T, int NTHREADS>
+// Low parts of rho, m, rho E of a double-float FP32 batch in global memory.
+template <typename T>
+struct BatchLo {
+  T* p[3];
+};
+
+template <typename T, int NTHREADS, bool DF>
 __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rho,
                                                               T* __restrict__ g_m,
                                                               T* __restrict__ g_en,
-                                                              T* __restrict__ g_ei,
+                                                              T* __restrict__ g_ei, BatchLo<T> lo,
                                                               InstDev* __restrict__ inst,
                                                               const int* __restrict__ order,
                                                               double gamma_d, double cfl,
@@ -684,9 +771,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_kernel(T* __restrict__ g_rh
   InstDev I = inst[id];
   if (I.done) return;
   const Part P{I.n, 0, 0, I.n, 0, I.n, true, true};
-  advance_part<T, NTHREADS, false>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
-                                   nmax + 2 * kBatchGhost, nmax + 1, gamma_d, cfl, max_steps,
-                                   red, nullptr);
+  advance_part<T, NTHREADS, false, DF>(g_rho, g_m, g_en, g_ei, lo.p, I, P, (T*)smem_raw,
+                                       nmax + 2 * kBatchGhost, nmax + 1, gamma_d, cfl, max_steps,
+                                       red, nullptr);
   if (threadIdx.x == 0) {  // thread 0's copy holds the instance's time
     if (I.t >= I.t_end) I.done = 1;
     inst[id] = I;
@@ -707,15 +794,16 @@ constexpr int kItemSplit = -2;
 // per step (pair_cfl_step).  Both CTAs of a split item take the same branch and the same
 // decisions, so they meet the same cluster barriers; the CTAs of a two-instance item
 // never wait on each other.  A split instance needs n >= 2 kPairHalo.
-template <typename T, int NTHREADS>
+template <typename T, int NTHREADS, bool DF>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     batch_cluster_kernel(T* __restrict__ g_rho, T* __restrict__ g_m, T* __restrict__ g_en,
-                         T* __restrict__ g_ei, InstDev* __restrict__ inst,
+                         T* __restrict__ g_ei, BatchLo<T> lo, InstDev* __restrict__ inst,
                          const int2* __restrict__ items, double gamma_d, double cfl,
                          int max_steps, int nlmax, int nmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[80];
   __shared__ T xslot[2][kPairSlot];
+  T* const* g_lo = lo.p;
   const int rank = (int)cluster_rank();
   const int2 item = items[blockIdx.x >> 1];
   if (item.y == kItemSplit) {
@@ -725,7 +813,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const int n = I.n, n0 = n / 2;
     const Part P = rank == 0 ? Part{n0, 0, 0, n0 + 3, 0, n0 + 3, true, false}
                              : Part{n - n0, n0, -3, n - n0, -3, n - n0, false, true};
-    advance_part<T, NTHREADS, true>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
+    advance_part<T, NTHREADS, true, DF>(g_rho, g_m, g_en, g_ei, g_lo, I, P, (T*)smem_raw,
                                     nlmax + 2 * kPairHalo, nlmax + 8, gamma_d, cfl, max_steps,
                                     red, &xslot[0][0]);
     if (rank == 0 && threadIdx.x == 0) {  // both CTAs hold the same time; rank 0 stores it
@@ -738,7 +826,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     InstDev I = inst[id];
     if (I.done) return;
     const Part P{I.n, 0, 0, I.n, 0, I.n, true, true};
-    advance_part<T, NTHREADS, false>(g_rho, g_m, g_en, g_ei, I, P, (T*)smem_raw,
+    advance_part<T, NTHREADS, false, DF>(g_rho, g_m, g_en, g_ei, g_lo, I, P, (T*)smem_raw,
                                      nmax + 2 * kBatchGhost, nmax + 1, gamma_d, cfl, max_steps,
                                      red, nullptr);
     if (threadIdx.x == 0) {

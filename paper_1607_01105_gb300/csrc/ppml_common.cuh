@@ -26,6 +26,10 @@ template <typename T>
 struct MarchArgs {
   const T* u[6];  // input fields
   T* out[6];      // output fields (out[0] NULL: rho is not written)
+  // FP32 double-float states: low parts of rho, m_x, m_y, m_z, rho E of the input and the
+  // output (all NULL for plain FP32 and FP64 states; outlo[0] NULL when out[0] is)
+  const T* ulo[5];
+  T* outlo[5];
   const T* phi;   // optional potential (Eulerian stage)
   GridGeom g;
   double h[3];
@@ -183,6 +187,11 @@ struct FieldSums<float> {
 #pragma unroll
     for (int f = 0; f < 6; f++) s[f].add(u[f]);
   }
+  // low parts of a double-float state's fields 0..4 (below the sums' rounding: plain adds)
+  __device__ __forceinline__ void add_lo(const float lo[5]) {
+#pragma unroll
+    for (int f = 0; f < 5; f++) s[f].lo += lo[f];
+  }
   __device__ __forceinline__ void get(double out[6]) const {
 #pragma unroll
     for (int f = 0; f < 6; f++) out[f] = s[f].value();
@@ -260,6 +269,14 @@ __global__ void __launch_bounds__(NT) diag_kernel(MarchArgs<T> A) {
 #pragma unroll
     for (int f = 0; f < 6; f++) u[f] = A.u[f][idx];
     sums.add(u);
+    if constexpr (sizeof(T) == 4) {
+      if (A.ulo[0]) {  // double-float state: the sums take the low parts too
+        float lo[5];
+#pragma unroll
+        for (int f = 0; f < 5; f++) lo[f] = A.ulo[f][idx];
+        sums.add_lo(lo);
+      }
+    }
     cell_speeds<T>(u, gamma, gm1, vmax, cmax, nbad);
   }
   double sd[6];

@@ -232,6 +232,53 @@ __device__ __forceinline__ float internal_energy_ff(float rho, float mx, float m
   return d + (de - ql);
 }
 
+// ------------------------------------------------------------ double-float state values
+// A field stored as an unevaluated float pair (hi, lo), |lo| <= ulp(hi) / 2, carries about
+// 48 significant bits.  The FP32 path keeps rho, m and rho E this way when the caller
+// supplies the low parts: the stencil arithmetic reads hi, and every update of a stored
+// value and the Sec. 1.4 difference rho E - |m|^2 / (2 rho) use both parts.
+
+// (hi, lo) = (h + l) - d, renormalised (TwoSum of h and -d, then the low terms).
+__device__ __forceinline__ void df_sub(float h, float l, float d, float& hi, float& lo) {
+  float s, e;
+  two_sum(h, -d, s, e);
+  e += l;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Split a double into its float pair.
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// rho eps = (eh + el) - |m|^2 / (2 rho) with rho = rh + rl and m_a = mh_a + ml_a, in
+// double-float (about 44 significant bits), rounded once to float.  Sec. 1.4 (dense
+// branch) on double-float totals: the error of the difference does not grow with the
+// ratio of kinetic to internal energy beyond the double-float rounding.
+__device__ __forceinline__ float internal_energy_df(float rh, float rl, const float mh[3],
+                                                    const float ml[3], float eh, float el) {
+  float p[3], e[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    p[a] = mh[a] * mh[a];
+    e[a] = fmaf(mh[a], mh[a], -p[a]) + 2.0f * mh[a] * ml[a];  // ml^2 is below 2^-48 |m|^2
+  }
+  float s, t1, hi, t2;
+  two_sum(p[0], p[1], s, t1);
+  two_sum(s, p[2], hi, t2);
+  const float lo = ((t1 + t2) + (e[0] + e[1])) + e[2];  // |m|^2 = hi + lo
+  const float r2 = 2.0f * rh, r2l = 2.0f * rl;            // 2 rho = r2 + r2l exactly
+  const float ir2 = rcp_approx(r2);
+  const float q = hi * ir2;
+  const float rem = (fmaf(-q, r2, hi) - q * r2l) + lo;  // hi + lo - q (r2 + r2l)
+  const float ql = rem * ir2;                           // |m|^2 / (2 rho) = q + ql
+  float d, de;
+  two_sum(eh, -q, d, de);
+  return d + ((de + el) - ql);
+}
+
 // Neumaier-compensated running sum in float; value() = hi + lo in double.
 struct CompSum {
   float hi, lo;
@@ -274,6 +321,24 @@ __device__ __forceinline__ void vacuum_correct_f32(float u[6], double rho_vac) {
   u[1] = (float)d[1];
   u[2] = (float)d[2];
   u[3] = (float)d[3];
+  u[5] = (float)d[5];
+}
+// The same two branches on a double-float state (low parts ul of rho, m, rho E): the dense
+// value of rho eps, and the vacuum branch in double on hi + lo (m's pairs and rho eps
+// rewritten).
+__device__ __forceinline__ float dense_eps_df(const float u[6], const float ul[5]) {
+  const float mh[3] = {u[1], u[2], u[3]}, ml[3] = {ul[1], ul[2], ul[3]};
+  const float e = internal_energy_df(u[0], ul[0], mh, ml, u[4], ul[4]);
+  return e > 0.f ? e : u[5];
+}
+__device__ __forceinline__ void vacuum_correct_df(float u[6], float ul[5], double rho_vac) {
+  double d[6];
+#pragma unroll
+  for (int f = 0; f < 5; f++) d[f] = (double)u[f] + (double)ul[f];
+  d[5] = u[5];
+  energy_correction(d, rho_vac);
+#pragma unroll
+  for (int a = 1; a <= 3; a++) df_split(d[a], u[a], ul[a]);
   u[5] = (float)d[5];
 }
 __device__ __forceinline__ int correct_energy_f32(float u[6], float rho_vac_up, double rho_vac) {

@@ -107,6 +107,7 @@ struct ppml_grid {
   GridGeom geom;
   size_t elt;
   void* ustar[6];  // [0] unused (rho is not changed by the Eulerian stage)
+  void* ustar_lo[5];  // FP32: low parts of U*'s m and rho E ([0] unused)
   Partial* partials;
   int nblk_march, nblk_diag, npartials;
   int tiles_x, tiles_y, tiles_z;
@@ -166,6 +167,28 @@ int ppml_validate_state(const ppml_state* u, const char* what) {
     if (((uintptr_t)u->f[f]) & 15u)
       return ppml_fail(PPML_E_INVAL, "%s field %d is not 16-byte aligned", what, f);
   }
+  const int nlo = ppml_state_has_lo(u);
+  if (nlo != 0 && nlo != 5)
+    return ppml_fail(PPML_E_INVAL, "%s has %d of 5 low-part pointers (all or none)", what, nlo);
+  for (int f = 0; f < 5 && nlo; f++) {
+    if (((uintptr_t)u->lo[f]) & 15u)
+      return ppml_fail(PPML_E_INVAL, "%s low part %d is not 16-byte aligned", what, f);
+    for (int q = 0; q < 6; q++)
+      if (u->lo[f] == u->f[q]) return ppml_fail(PPML_E_INVAL, "%s low part %d aliases a field", what, f);
+  }
+  return PPML_OK;
+}
+
+int ppml_state_has_lo(const ppml_state* u) {
+  int n = 0;
+  for (int f = 0; f < 5; f++) n += u->lo[f] != nullptr;
+  return n;
+}
+
+// A state of the grid's type: low parts only in FP32.
+static int check_state_type(const ppml_grid_desc* d, const ppml_state* u, const char* what) {
+  if (d->dtype == PPML_F64 && ppml_state_has_lo(u))
+    return ppml_fail(PPML_E_INVAL, "%s: low parts are for FP32 states only", what);
   return PPML_OK;
 }
 
@@ -194,6 +217,7 @@ template <typename T>
 int run_diag(ppml_grid* g, const ppml_state* u, cudaStream_t st) {
   MarchArgs<T> A = make_args<T>(g, 0.0, nullptr);
   for (int f = 0; f < 6; f++) A.u[f] = (const T*)u->f[f];
+  for (int f = 0; f < 5; f++) A.ulo[f] = (const T*)u->lo[f];
   int rc = launch_diag<T>(A, g->nblk_diag, st);
   if (rc) return rc;
   return launch_finalize(g->partials, g->nblk_diag, g->dev, g->d.cfl, g->hmin, g->vol,
@@ -201,13 +225,18 @@ int run_diag(ppml_grid* g, const ppml_state* u, cudaStream_t st) {
 }
 
 template <typename T>
-int run_eulerian(ppml_grid* g, const ppml_state* u, void* const out[6], const T* phi,
-                 double dt_host, const double* dt_dev, cudaStream_t st) {
+int run_eulerian(ppml_grid* g, const ppml_state* u, void* const out[6], void* const outlo[5],
+                 const T* phi, double dt_host, const double* dt_dev, cudaStream_t st) {
   MarchArgs<T> A = make_args<T>(g, dt_host, dt_dev);
   for (int f = 0; f < 6; f++) {
     A.u[f] = (const T*)u->f[f];
     A.out[f] = (T*)out[f];
   }
+  if (ppml_state_has_lo(u))
+    for (int f = 0; f < 5; f++) {
+      A.ulo[f] = (const T*)u->lo[f];
+      A.outlo[f] = (T*)outlo[f];
+    }
   A.phi = phi;
   return launch_eulerian<T>(A, g->nblk_march, st);
 }
@@ -243,13 +272,19 @@ int run_step(ppml_grid* g, const ppml_state* uin, ppml_state* uout, const T* phi
     cudaEventRecord(ev[0], st);
   }
   void* star[6] = {nullptr, g->ustar[1], g->ustar[2], g->ustar[3], g->ustar[4], g->ustar[5]};
-  int rc = run_eulerian<T>(g, uin, star, phi, dt_host, dt_dev, st);
+  void* star_lo[5] = {nullptr, g->ustar_lo[1], g->ustar_lo[2], g->ustar_lo[3], g->ustar_lo[4]};
+  int rc = run_eulerian<T>(g, uin, star, star_lo, phi, dt_host, dt_dev, st);
   if (rc) return rc;
   if (ev) cudaEventRecord(ev[1], st);
   MarchArgs<T> L = make_args<T>(g, dt_host, dt_dev);
   L.u[0] = (const T*)uin->f[0];
   for (int f = 1; f < 6; f++) L.u[f] = (const T*)g->ustar[f];
   for (int f = 0; f < 6; f++) L.out[f] = (T*)uout->f[f];
+  if (ppml_state_has_lo(uin)) {
+    L.ulo[0] = (const T*)uin->lo[0];
+    for (int f = 1; f < 5; f++) L.ulo[f] = (const T*)g->ustar_lo[f];
+    for (int f = 0; f < 5; f++) L.outlo[f] = (T*)uout->lo[f];
+  }
   rc = launch_lagrangian<T>(L, g->nblk_march, st);
   if (rc) return rc;
   if (ev) cudaEventRecord(ev[2], st);
@@ -269,6 +304,8 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
   int rc = ppml_validate_desc(d);
   if (rc) return rc;
   rc = ppml_validate_state(u0, "u0");
+  if (rc) return rc;
+  rc = check_state_type(d, u0, "u0");
   if (rc) return rc;
   ppml_grid* g = new (std::nothrow) ppml_grid();
   if (!g) return ppml_fail(PPML_E_NOMEM, "host allocation failed");
@@ -305,6 +342,12 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
       return ppml_fail(PPML_E_NOMEM, "cudaMalloc of U* (%zu bytes) failed", fbytes);
     }
   }
+  for (int f = 1; f < 5 && d->dtype == PPML_F32; f++) {
+    if (cudaMalloc(&g->ustar_lo[f], fbytes) != cudaSuccess) {
+      ppml_free_grid(g);
+      return ppml_fail(PPML_E_NOMEM, "cudaMalloc of U* low parts (%zu bytes) failed", fbytes);
+    }
+  }
   if (cudaMalloc(&g->partials, sizeof(Partial) * (size_t)g->npartials) != cudaSuccess ||
       cudaMalloc(&g->dev, sizeof(DevScalars)) != cudaSuccess) {
     ppml_free_grid(g);
@@ -335,6 +378,8 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
   cudaDeviceSynchronize();
   for (int f = 0; f < 6; f++)
     if (g->ustar[f]) cudaFree(g->ustar[f]);
+  for (int f = 0; f < 5; f++)
+    if (g->ustar_lo[f]) cudaFree(g->ustar_lo[f]);
   if (g->partials) cudaFree(g->partials);
   if (g->dev) cudaFree(g->dev);
   if (g->ev) {
@@ -433,6 +478,8 @@ extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, v
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
   int rc = ppml_validate_state(u, "u");
   if (rc) return rc;
+  rc = check_state_type(&g->d, u, "u");
+  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   rc = g->d.dtype == PPML_F64 ? run_diag<double>(g, u, st) : run_diag<float>(g, u, st);
   if (rc) return rc;
@@ -447,6 +494,31 @@ extern "C" int ppml_cfl_dt(ppml_grid* g, const ppml_state* u, double* dt_host, v
 
 static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, const void* phi,
                        double dt, void* stream);
+
+// An input and an output state of one call: the grid's type, low parts in both or neither,
+// and no array of one in the other.
+static int check_state_pair(const ppml_grid_desc* d, const ppml_state* a, const ppml_state* b) {
+  int rc = check_state_type(d, a, "u_in");
+  if (rc) return rc;
+  rc = check_state_type(d, b, "u_out");
+  if (rc) return rc;
+  if ((ppml_state_has_lo(a) != 0) != (ppml_state_has_lo(b) != 0))
+    return ppml_fail(PPML_E_INVAL, "u_in and u_out must both carry low parts or neither");
+  const void* pa[11];
+  const void* pb[11];
+  for (int f = 0; f < 6; f++) {
+    pa[f] = a->f[f];
+    pb[f] = b->f[f];
+  }
+  for (int f = 0; f < 5; f++) {
+    pa[6 + f] = a->lo[f];
+    pb[6 + f] = b->lo[f];
+  }
+  for (int i = 0; i < 11; i++)
+    for (int j = 0; j < 11; j++)
+      if (pa[i] && pa[i] == pb[j]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");
+  return PPML_OK;
+}
 
 extern "C" int ppml_step(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, double dt,
                          void* stream) {
@@ -470,9 +542,8 @@ static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, 
   if (rc) return rc;
   rc = ppml_validate_state(u_out, "u_out");
   if (rc) return rc;
-  for (int f = 0; f < 6; f++)
-    for (int q = 0; q < 6; q++)
-      if (u_in->f[f] == u_out->f[q]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");
+  rc = check_state_pair(&g->d, u_in, u_out);
+  if (rc) return rc;
   if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
   const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
   cudaStream_t st = (cudaStream_t)stream;
@@ -489,12 +560,14 @@ extern "C" int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_st
   if (rc) return rc;
   rc = ppml_validate_state(u_star, "u_star");
   if (rc) return rc;
+  rc = check_state_pair(&g->d, u_in, u_star);
+  if (rc) return rc;
   if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
   const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
   cudaStream_t st = (cudaStream_t)stream;
   return g->d.dtype == PPML_F64
-             ? run_eulerian<double>(g, u_in, u_star->f, nullptr, dt, dt_dev, st)
-             : run_eulerian<float>(g, u_in, u_star->f, nullptr, dt, dt_dev, st);
+             ? run_eulerian<double>(g, u_in, u_star->f, u_star->lo, nullptr, dt, dt_dev, st)
+             : run_eulerian<float>(g, u_in, u_star->f, u_star->lo, nullptr, dt, dt_dev, st);
 }
 
 extern "C" int ppml_conserved_sums(ppml_grid* g, const ppml_state* u, double out[6],
@@ -502,6 +575,8 @@ extern "C" int ppml_conserved_sums(ppml_grid* g, const ppml_state* u, double out
   ppml_clear_error();
   if (!g || !out) return ppml_fail(PPML_E_INVAL, "grid or out is NULL");
   int rc = ppml_validate_state(u, "u");
+  if (rc) return rc;
+  rc = check_state_type(&g->d, u, "u");
   if (rc) return rc;
   // Sums go through the same partial/finalize path; the handle's scalars are restored.
   DevScalars keep, hs;

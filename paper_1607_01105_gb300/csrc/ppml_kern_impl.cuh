@@ -20,16 +20,26 @@ struct MinBlocks<double> {
 };
 }  // namespace
 
-template <>
-int prepare_kernels<PPML_REAL>() {
+// Double-float states (low parts of rho, m, rho E) exist only in the FP32 path.
+constexpr bool kHasDF = sizeof(PPML_REAL) == 4;
+
+template <bool DF>
+cudaError_t set_stage_smem() {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  cudaError_t e = cudaFuncSetAttribute(lagrangian_tile<PPML_REAL, MB>,
+  cudaError_t e = cudaFuncSetAttribute(lagrangian_tile<PPML_REAL, MB, DF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(LagTileSmem<PPML_REAL>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eulerian_tile<PPML_REAL, MB>,
+    e = cudaFuncSetAttribute(eulerian_tile<PPML_REAL, MB, DF>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(EulTileSmem<PPML_REAL>));
+  return e;
+}
+
+template <>
+int prepare_kernels<PPML_REAL>() {
+  cudaError_t e = set_stage_smem<false>();
+  if (e == cudaSuccess && kHasDF) e = set_stage_smem<kHasDF>();
   if (e != cudaSuccess) return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   return PPML_OK;
 }
@@ -37,14 +47,20 @@ int prepare_kernels<PPML_REAL>() {
 template <>
 int launch_eulerian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  eulerian_tile<PPML_REAL, MB><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
+  if (kHasDF && A.outlo[1])
+    eulerian_tile<PPML_REAL, MB, kHasDF><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
+  else
+    eulerian_tile<PPML_REAL, MB, false><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
   return ppml_check_launch("eulerian_tile");
 }
 
 template <>
 int launch_lagrangian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  lagrangian_tile<PPML_REAL, MB><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
+  if (kHasDF && A.outlo[0])
+    lagrangian_tile<PPML_REAL, MB, kHasDF><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
+  else
+    lagrangian_tile<PPML_REAL, MB, false><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
   return ppml_check_launch("lagrangian_tile");
 }
 
@@ -88,38 +104,67 @@ int launch_poisson_symbol<PPML_REAL>(void* spec, const double* tx, const double*
 }
 
 namespace {
-template <int NT>
-int launch_batch_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei, InstDev* inst,
-                    const int* order, double gamma, double cfl, int max_steps, int nmax,
-                    int ninst, size_t smem, cudaStream_t st) {
-  static size_t configured = 0;
+// Opt-in shared memory of a kernel, raised once to the largest size launched so far.
+template <typename K>
+int raise_smem(K kernel, size_t smem, size_t& configured) {
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<PPML_REAL, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess)
       return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     configured = smem;
   }
-  batch_kernel<PPML_REAL, NT><<<ninst, NT, smem, st>>>(rho, m, en, ei, inst, order, gamma, cfl,
-                                                       max_steps, nmax);
+  return PPML_OK;
+}
+
+template <int NT, bool DF>
+int launch_batch_ntd(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                     BatchLo<PPML_REAL> lo, InstDev* inst, const int* order, double gamma,
+                     double cfl, int max_steps, int nmax, int ninst, size_t smem,
+                     cudaStream_t st) {
+  static size_t configured = 0;
+  int rc = raise_smem(batch_kernel<PPML_REAL, NT, DF>, smem, configured);
+  if (rc) return rc;
+  batch_kernel<PPML_REAL, NT, DF><<<ninst, NT, smem, st>>>(rho, m, en, ei, lo, inst, order, gamma,
+                                                           cfl, max_steps, nmax);
   return ppml_check_launch("batch_kernel");
 }
 
-template <int NT>
-int launch_cluster_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei, InstDev* inst,
-                      const int2* items, double gamma, double cfl, int max_steps, int nlmax,
-                      int nmax, int nitems, size_t smem, cudaStream_t st) {
+template <int NT, bool DF>
+int launch_cluster_ntd(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                       BatchLo<PPML_REAL> lo, InstDev* inst, const int2* items, double gamma,
+                       double cfl, int max_steps, int nlmax, int nmax, int nitems, size_t smem,
+                       cudaStream_t st) {
   static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_cluster_kernel<PPML_REAL, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-      return ppml_fail(PPML_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    configured = smem;
-  }
-  batch_cluster_kernel<PPML_REAL, NT><<<2 * nitems, NT, smem, st>>>(
-      rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax, nmax);
+  int rc = raise_smem(batch_cluster_kernel<PPML_REAL, NT, DF>, smem, configured);
+  if (rc) return rc;
+  batch_cluster_kernel<PPML_REAL, NT, DF><<<2 * nitems, NT, smem, st>>>(
+      rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps, nlmax, nmax);
   return ppml_check_launch("batch_cluster_kernel");
+}
+
+// double-float launches (low parts given) exist only in FP32
+template <int NT>
+int launch_batch_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                    BatchLo<PPML_REAL> lo, InstDev* inst, const int* order, double gamma,
+                    double cfl, int max_steps, int nmax, int ninst, size_t smem, cudaStream_t st) {
+  if (kHasDF && lo.p[0])
+    return launch_batch_ntd<NT, kHasDF>(rho, m, en, ei, lo, inst, order, gamma, cfl, max_steps,
+                                        nmax, ninst, smem, st);
+  return launch_batch_ntd<NT, false>(rho, m, en, ei, lo, inst, order, gamma, cfl, max_steps, nmax,
+                                     ninst, smem, st);
+}
+
+template <int NT>
+int launch_cluster_nt(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
+                      BatchLo<PPML_REAL> lo, InstDev* inst, const int2* items, double gamma,
+                      double cfl, int max_steps, int nlmax, int nmax, int nitems, size_t smem,
+                      cudaStream_t st) {
+  if (kHasDF && lo.p[0])
+    return launch_cluster_ntd<NT, kHasDF>(rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps,
+                                          nlmax, nmax, nitems, smem, st);
+  return launch_cluster_ntd<NT, false>(rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps,
+                                       nlmax, nmax, nitems, smem, st);
 }
 }  // namespace
 
@@ -133,18 +178,18 @@ int launch_batch_vacuum<PPML_REAL>(const PPML_REAL* rho, InstDev* inst, int nins
 
 template <>
 int launch_batch_cluster<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
-                                    InstDev* inst, const int2* items, double gamma, double cfl,
-                                    int max_steps, int nlmax, int nmax, int nitems, size_t smem,
-                                    int threads, cudaStream_t st) {
+                                    BatchLo<PPML_REAL> lo, InstDev* inst, const int2* items,
+                                    double gamma, double cfl, int max_steps, int nlmax, int nmax,
+                                    int nitems, size_t smem, int threads, cudaStream_t st) {
   switch (threads) {
     case 256:
-      return launch_cluster_nt<256>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+      return launch_cluster_nt<256>(rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps, nlmax,
                                     nmax, nitems, smem, st);
     case 512:
-      return launch_cluster_nt<512>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+      return launch_cluster_nt<512>(rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps, nlmax,
                                     nmax, nitems, smem, st);
     case 1024:
-      return launch_cluster_nt<1024>(rho, m, en, ei, inst, items, gamma, cfl, max_steps, nlmax,
+      return launch_cluster_nt<1024>(rho, m, en, ei, lo, inst, items, gamma, cfl, max_steps, nlmax,
                                      nmax, nitems, smem, st);
     default:
       return ppml_fail(PPML_E_INVAL, "batch CTA size %d is not 256, 512 or 1024", threads);
@@ -153,18 +198,18 @@ int launch_batch_cluster<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en,
 
 template <>
 int launch_batch<PPML_REAL>(PPML_REAL* rho, PPML_REAL* m, PPML_REAL* en, PPML_REAL* ei,
-                            InstDev* inst, const int* order, double gamma, double cfl,
-                            int max_steps, int nmax, int ninst, size_t smem, int threads,
-                            cudaStream_t st) {
+                            BatchLo<PPML_REAL> lo, InstDev* inst, const int* order, double gamma,
+                            double cfl, int max_steps, int nmax, int ninst, size_t smem,
+                            int threads, cudaStream_t st) {
   switch (threads) {
     case 256:
-      return launch_batch_nt<256>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax, ninst,
+      return launch_batch_nt<256>(rho, m, en, ei, lo, inst, order, gamma, cfl, max_steps, nmax, ninst,
                                   smem, st);
     case 512:
-      return launch_batch_nt<512>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax, ninst,
+      return launch_batch_nt<512>(rho, m, en, ei, lo, inst, order, gamma, cfl, max_steps, nmax, ninst,
                                   smem, st);
     case 1024:
-      return launch_batch_nt<1024>(rho, m, en, ei, inst, order, gamma, cfl, max_steps, nmax,
+      return launch_batch_nt<1024>(rho, m, en, ei, lo, inst, order, gamma, cfl, max_steps, nmax,
                                    ninst, smem, st);
     default:
       return ppml_fail(PPML_E_INVAL, "batch CTA size %d is not 256, 512 or 1024", threads);

@@ -28,13 +28,13 @@ int launch_poisson_symbol(void* spec, const double* tx, const double* ty, const 
 template <typename T>
 int launch_batch_vacuum(const T* rho, InstDev* inst, int ninst, cudaStream_t st);
 template <typename T>
-int launch_batch(T* rho, T* m, T* en, T* ei, InstDev* inst, const int* order, double gamma,
-                 double cfl, int max_steps, int nmax, int ninst, size_t smem, int threads,
-                 cudaStream_t st);
+int launch_batch(T* rho, T* m, T* en, T* ei, BatchLo<T> lo, InstDev* inst, const int* order,
+                 double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem,
+                 int threads, cudaStream_t st);
 template <typename T>
-int launch_batch_cluster(T* rho, T* m, T* en, T* ei, InstDev* inst, const int2* items,
-                         double gamma, double cfl, int max_steps, int nlmax, int nmax,
-                         int nitems, size_t smem, int threads, cudaStream_t st);
+int launch_batch_cluster(T* rho, T* m, T* en, T* ei, BatchLo<T> lo, InstDev* inst,
+                         const int2* items, double gamma, double cfl, int max_steps, int nlmax,
+                         int nmax, int nitems, size_t smem, int threads, cudaStream_t st);
 
 // Deterministic reduction of per-CTA partials into the step scalars (ppml_grid.cu).
 int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
@@ -57,11 +57,11 @@ int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, doubl
   template <>                                                                                \
   int launch_batch_vacuum<R>(const R* rho, InstDev* inst, int ninst, cudaStream_t st);        \
   template <>                                                                                \
-  int launch_batch<R>(R * rho, R * m, R * en, R * ei, InstDev * inst, const int* order,       \
-                      double gamma, double cfl, int max_steps, int nmax, int ninst, size_t smem, \
-                      int threads, cudaStream_t st);                                           \
+  int launch_batch<R>(R * rho, R * m, R * en, R * ei, BatchLo<R> lo, InstDev * inst,          \
+                      const int* order, double gamma, double cfl, int max_steps, int nmax,     \
+                      int ninst, size_t smem, int threads, cudaStream_t st);                   \
   template <>                                                                                \
-  int launch_batch_cluster<R>(R * rho, R * m, R * en, R * ei, InstDev * inst,                 \
+  int launch_batch_cluster<R>(R * rho, R * m, R * en, R * ei, BatchLo<R> lo, InstDev * inst,  \
                               const int2* items, double gamma, double cfl, int max_steps,      \
                               int nlmax, int nmax, int nitems, size_t smem, int threads,       \
                               cudaStream_t st);

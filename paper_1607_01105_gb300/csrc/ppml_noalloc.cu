@@ -150,6 +150,11 @@ extern "C" int ppml_step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in
   if (rc) return rc;
   rc = ppml_validate_state(u_out, "u_out");
   if (rc) return rc;
+  if (ppml_state_has_lo(u_in) || ppml_state_has_lo(u_out))
+    return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc takes plain float or double states "
+                                   "(no low parts)");
+  if (d->t_end > 0.0)
+    return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc keeps no simulated time: t_end must be 0");
   for (int f = 0; f < 6; f++)
     for (int q = 0; q < 6; q++)
       if (u_in->f[f] == u_out->f[q]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");

@@ -293,11 +293,15 @@ __device__ __forceinline__ void stage_box_fast(T* box, const T* __restrict__ src
 // 1: acc += div; 2: dst[c gs] = core - (acc + div) for c < nvalid (acc only if have_acc).
 // The pipeline forms, when position p arrives, the slope at p-1, the face at p-3/2, the
 // parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
-// peeled and the steady state is a loop unrolled by two.
-template <typename T, int MODE, bool FLAT>
+// peeled and the steady state is a loop unrolled by two.  DF (MODE 2): when dstlo is
+// non-NULL the field is a double-float value whose low part srclo[c gs] is read and the
+// update is added in double-float (dst the high part, dstlo the low part).
+template <typename T, int MODE, bool FLAT, bool DF = false>
 __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, const T* vh, T th,
                                          double tau, double h, T* acc, bool have_acc,
-                                         T* __restrict__ dst, long long gs, int nvalid) {
+                                         T* __restrict__ dst, long long gs, int nvalid,
+                                         const T* __restrict__ srclo = nullptr,
+                                         T* __restrict__ dstlo = nullptr) {
   T qa = halo[0], qb = halo[SLP];  // q(p-2), q(p-1)
   T qn = halo[2 * SLP];            // p = -1
   T da = limited_slope(qa, qb, qn);
@@ -347,7 +351,19 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
     } else if (MODE == 1) {
       acc[o] = acc[o] + d;
     } else if (c < nvalid) {
-      dst[gs * c] = core[o] - (have_acc ? acc[o] + d : d);
+      const T upd = have_acc ? acc[o] + d : d;
+      if constexpr (DF) {
+        if (dstlo) {
+          float hi, lo;
+          df_sub(core[o], srclo[gs * c], upd, hi, lo);
+          dst[gs * c] = hi;
+          dstlo[gs * c] = lo;
+        } else {
+          dst[gs * c] = core[o] - upd;
+        }
+      } else {
+        dst[gs * c] = core[o] - upd;
+      }
     }
     Fp = F;
     PR = Pn.R;
@@ -398,7 +414,8 @@ __device__ __forceinline__ void line_face_velocities(const T* vb, const T* rb, i
   }
 }
 
-template <typename T, int MINB>
+// DF: the state is double-float (A.ulo / A.outlo give the low parts of rho, m, rho E).
+template <typename T, int MINB, bool DF>
 __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LagTileSmem<T>& S = *reinterpret_cast<LagTileSmem<T>*>(smem_raw);
@@ -577,10 +594,12 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       const int cs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
       const T* halo = &S.fld[halo_at(ax, 0, tid)];
       const T* vhl = &S.vh[ax][0][tid];
+      const T* srclo = DF && f < 5 ? A.ulo[f] + zline0 : nullptr;
+      T* dstlo = DF && f < 5 ? A.outlo[f] + zline0 : nullptr;
       if (first_order) {
         if (ax == 2)
-          lag_line<T, 2, true>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
-                               mode == 1, A.out[f] + zline0, g.nxy, nvalid_z);
+          lag_line<T, 2, true, DF>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
+                                   mode == 1, A.out[f] + zline0, g.nxy, nvalid_z, srclo, dstlo);
         else if (mode == 0)
           lag_line<T, 0, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
                                false, nullptr, 0, 0);
@@ -588,8 +607,8 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
           lag_line<T, 1, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
                                false, nullptr, 0, 0);
       } else if (ax == 2)
-        lag_line<T, 2, false>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
-                              mode == 1, A.out[f] + zline0, g.nxy, nvalid_z);
+        lag_line<T, 2, false, DF>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
+                                  mode == 1, A.out[f] + zline0, g.nxy, nvalid_z, srclo, dstlo);
       else if (mode == 0)
         lag_line<T, 0, false>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
                               false, nullptr, 0, 0);
@@ -602,7 +621,18 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
     if (!act[2]) {  // no z sweep: finish from the x/y part
       for (int c = 0; c < nvalid_z; c++) {
         const int o = acc_at(a, b, c);
-        A.out[f][zline0 + g.nxy * c] = S.fld[o] - (mode == 1 ? S.acc[o] : T(0));
+        const long long idx = zline0 + g.nxy * c;
+        const T upd = mode == 1 ? S.acc[o] : T(0);
+        if constexpr (DF) {
+          if (f < 5) {
+            float hi, lo;
+            df_sub(S.fld[o], A.ulo[f][idx], upd, hi, lo);
+            A.out[f][idx] = hi;
+            A.outlo[f][idx] = lo;
+            continue;
+          }
+        }
+        A.out[f][idx] = S.fld[o] - upd;
       }
     }
     __syncthreads();
@@ -614,46 +644,69 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   T vmax = T(0), cmax = T(0);
   unsigned long long nvac = 0, nbad = 0;
   const float rho_vac_up = __double2float_ru(A.rho_vac);
-  // groups of FB cells: all loads of a group are issued before its first store
+  // groups of FB cells: all loads of a group are issued before its first store.  The
+  // correction changes m only in vacuum cells, so only those store m back.
   constexpr int FB = 4;
 #pragma unroll 1
   for (int c0 = 0; c0 < nvalid_z; c0 += FB) {
     T u[FB][6];
+    T ul[FB][5];  // low parts (double-float states)
 #pragma unroll
-    for (int q = 0; q < FB; q++)
+    for (int q = 0; q < FB; q++) {
+      const long long idx = zline0 + g.nxy * (c0 + q);
+      const bool ok = c0 + q < nvalid_z;
 #pragma unroll
-      for (int f = 0; f < 6; f++)
-        u[q][f] = c0 + q < nvalid_z ? A.out[f][zline0 + g.nxy * (c0 + q)] : T(1);
+      for (int f = 0; f < 6; f++) u[q][f] = ok ? A.out[f][idx] : T(1);
+#pragma unroll
+      for (int f = 0; f < 5; f++) ul[q][f] = DF && ok ? A.outlo[f][idx] : T(0);
+    }
+    bool vac[FB];
     if constexpr (sizeof(T) == 4) {
       // the dense branch for every cell of the group without control flow (so that the
       // cells' chains interleave), then the rare vacuum cells on their stored values
-      bool vac[FB], any_vac = false;
+      bool any_vac = false;
 #pragma unroll
       for (int q = 0; q < FB; q++) {
         vac[q] = c0 + q < nvalid_z && vacuum_cell_f32(u[q], rho_vac_up);
         any_vac |= vac[q];
-        const float e = dense_eps_f32(u[q]);
+        const float e = DF ? dense_eps_df(u[q], ul[q]) : dense_eps_f32(u[q]);
         u[q][5] = vac[q] ? u[q][5] : e;
       }
       if (any_vac) {
 #pragma unroll
         for (int q = 0; q < FB; q++)
           if (vac[q]) {
-            vacuum_correct_f32(u[q], A.rho_vac);
+            if constexpr (DF)
+              vacuum_correct_df(u[q], ul[q], A.rho_vac);
+            else
+              vacuum_correct_f32(u[q], A.rho_vac);
             nvac++;
           }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < FB; q++) {
+        vac[q] = false;
+        if (c0 + q < nvalid_z) {
+          vac[q] = correct_energy<T>(u[q], A.rho_vac) != 0;
+          nvac += vac[q];
+        }
       }
     }
 #pragma unroll
     for (int q = 0; q < FB; q++) {
       if (c0 + q >= nvalid_z) break;
       const long long idx = zline0 + g.nxy * (c0 + q);
-      if constexpr (sizeof(T) != 4) nvac += correct_energy<T>(u[q], A.rho_vac);
-      A.out[1][idx] = u[q][1];
-      A.out[2][idx] = u[q][2];
-      A.out[3][idx] = u[q][3];
+      if (vac[q]) {
+#pragma unroll
+        for (int f = 1; f <= 3; f++) {
+          A.out[f][idx] = u[q][f];
+          if constexpr (DF) A.outlo[f][idx] = ul[q][f];
+        }
+      }
       A.out[5][idx] = u[q][5];
       sums.add(u[q]);
+      if constexpr (DF) sums.add_lo(ul[q]);
       if constexpr (sizeof(T) == 4)
         cell_speeds_f32(u[q], gamma, gm1, vmax, cmax, nbad);
       else
@@ -688,7 +741,9 @@ struct EulTileSmem {
 
 __device__ __forceinline__ int slab_at(int p, int a, int b) { return (p + TH) * SLP + a + TB * b; }
 
-template <typename T, int MINB>
+// DF: the state is double-float (A.ulo / A.outlo give the low parts of rho, m, rho E); the
+// momentum and total-energy updates are added in double-float.
+template <typename T, int MINB, bool DF>
 __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EulTileSmem<T>& S = *reinterpret_cast<EulTileSmem<T>*>(smem_raw);
@@ -767,7 +822,14 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       S.av[ai] = first ? dv : S.av[ai] + dv;
       if (in_domain(g, tg, i, j, k)) {
         const long long idx = (long long)(tg.i0 + i) + (long long)g.n[0] * (tg.j0 + j) + g.nxy * (tg.k0 + k);
-        A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
+        if constexpr (DF) {
+          float hi, lo;
+          df_sub(S.m[slab_at(c, a, b)], A.ulo[1 + ax][idx], dm, hi, lo);
+          A.out[1 + ax][idx] = hi;
+          A.outlo[1 + ax][idx] = lo;
+        } else {
+          A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
+        }
       }
     };
     auto vq = [&](int p) {
@@ -794,6 +856,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       if (!in_domain(g, tg, a, b, c)) continue;
       const long long idx = (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * (tg.k0 + c);
       A.out[1 + ax][idx] = A.u[1 + ax][idx];
+      if constexpr (DF) A.outlo[1 + ax][idx] = A.ulo[1 + ax][idx];
     }
   }
   __syncthreads();
@@ -802,18 +865,26 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     constexpr int EB = 8;
 #pragma unroll 1
     for (int c0 = 0; c0 < TB; c0 += EB) {
-      T en[EB], ei[EB];
+      T en[EB], ei[EB], el[EB];
 #pragma unroll
       for (int q = 0; q < EB; q++) {
         const long long idx = zline0e + g.nxy * (c0 + q);
         en[q] = A.u[4][idx];
         ei[q] = A.u[5][idx];
+        if constexpr (DF) el[q] = A.ulo[4][idx];
       }
 #pragma unroll
       for (int q = 0; q < EB; q++) {
         const long long idx = zline0e + g.nxy * (c0 + q);
         const int ai = acc_at(a, b, c0 + q);
-        A.out[4][idx] = en[q] - S.apv[ai];
+        if constexpr (DF) {
+          float hi, lo;
+          df_sub(en[q], el[q], S.apv[ai], hi, lo);
+          A.out[4][idx] = hi;
+          A.outlo[4][idx] = lo;
+        } else {
+          A.out[4][idx] = en[q] - S.apv[ai];
+        }
         A.out[5][idx] = ei[q] - gm1 * ei[q] * S.av[ai];
       }
     }
@@ -828,6 +899,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     const T dpvs = first ? T(0) : S.apv[acc_at(a, b, c)];
     const T dvs = first ? T(0) : S.av[acc_at(a, b, c)];
     T en = A.u[4][idx] - dpvs;
+    T den = dpvs;  // DF: the whole FP32 decrement of rho E, added to the pair once
     if (A.phi) {
       GridGeom gp = g;  // Phi: zero-gradient at reflecting walls, like at outflow faces
       for (int q = 0; q < 6; q++)
@@ -841,15 +913,33 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         const T pp = load_bc(A.phi, -1, gi + di, gj + dj, gk + dk, gp);
         const T pm = load_bc(A.phi, -1, gi - di, gj - dj, gk - dk, gp);
         const T grad = (pp - pm) / T(2.0 * A.h[ax]);
-        m[ax] -= T(tau) * rho0 * grad;
-        en -= T(tau) * m0[ax] * grad;
+        if constexpr (DF) {
+          float hi, lo;
+          df_sub(m[ax], A.outlo[1 + ax][idx], T(tau) * rho0 * grad, hi, lo);
+          m[ax] = hi;
+          A.outlo[1 + ax][idx] = lo;
+          den += T(tau) * m0[ax] * grad;
+        } else {
+          m[ax] -= T(tau) * rho0 * grad;
+          en -= T(tau) * m0[ax] * grad;
+        }
       }
       A.out[1][idx] = m[0];
       A.out[2][idx] = m[1];
       A.out[3][idx] = m[2];
     }
-    if (A.out[0]) A.out[0][idx] = rho0;
-    A.out[4][idx] = en;
+    if (A.out[0]) {
+      A.out[0][idx] = rho0;
+      if constexpr (DF) A.outlo[0][idx] = A.ulo[0][idx];
+    }
+    if constexpr (DF) {
+      float hi, lo;
+      df_sub(A.u[4][idx], A.ulo[4][idx], den, hi, lo);
+      A.out[4][idx] = hi;
+      A.outlo[4][idx] = lo;
+    } else {
+      A.out[4][idx] = en;
+    }
     A.out[5][idx] = ei0 - gm1 * ei0 * dvs;
   }
 }

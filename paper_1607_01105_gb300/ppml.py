@@ -43,7 +43,7 @@ class GridDesc(ctypes.Structure):
 
 
 class State(ctypes.Structure):
-    _fields_ = [("f", ctypes.c_void_p * 6)]
+    _fields_ = [("f", ctypes.c_void_p * 6), ("lo", ctypes.c_void_p * 5)]
 
 
 class Diag(ctypes.Structure):
@@ -66,8 +66,10 @@ _lib.ppml_dt_device.restype = _vp
 _lib.ppml_batch_init.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]
-_lib.ppml_batch_step.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
-_lib.ppml_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]
+_lib.ppml_batch_step.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int), _vp]
+_lib.ppml_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_uint), _vp]
 _lib.ppml_batch_free.argtypes = [_vp]
 _lib.ppml_last_error.restype = ctypes.c_char_p
 _lib.ppml_profile.argtypes = [_vp, ctypes.c_int]
@@ -115,8 +117,10 @@ def torch_dtype(dtype: int):
 
 
 def _state(fields, dtype=None, shape=None) -> State:
-    if len(fields) != 6:
-        raise ValueError("a state has six fields")
+    """Six fields, or eleven: the six and the low parts of rho, m_x, m_y, m_z, rho E of a
+    double-float FP32 state."""
+    if len(fields) not in (6, 11):
+        raise ValueError("a state has six fields (or six and five low parts)")
     s = State()
     for i, t in enumerate(fields):
         if not t.is_cuda or not t.is_contiguous():
@@ -125,7 +129,10 @@ def _state(fields, dtype=None, shape=None) -> State:
             raise ValueError(f"field {i} has dtype {t.dtype}, expected {dtype}")
         if shape is not None and t.numel() != shape:
             raise ValueError(f"field {i} has {t.numel()} elements, expected {shape}")
-        s.f[i] = t.data_ptr()
+        if i < 6:
+            s.f[i] = t.data_ptr()
+        else:
+            s.lo[i - 6] = t.data_ptr()
     return s
 
 
@@ -322,17 +329,35 @@ class Batch:
     def set_threads(self, threads):
         _check(_lib.ppml_batch_set_threads(self._h, int(threads)))
 
-    def step(self, fields, max_steps, sync=False, stream=None):
+    def step(self, fields, max_steps, sync=False, stream=None, lo=None):
+        """Advance the batch; `lo`: None or three tensors with the low parts of rho, m,
+        rho E (FP32).  With sync, returns the number of instances at their end time."""
         ptrs = self._ptrs(fields)
+        lptr = None
+        if lo is not None:
+            if len(lo) != 3:
+                raise ValueError("three low-part arrays")
+            lptr = (ctypes.c_void_p * 3)()
+            for i, t in enumerate(lo):
+                if not t.is_cuda or not t.is_contiguous() or t.dtype != self.tdtype or t.numel() != self.total:
+                    raise ValueError(f"low part {i} has the wrong device, layout, dtype or size")
+                lptr[i] = t.data_ptr()
         done = ctypes.c_int(-1)
-        _check(_lib.ppml_batch_step(self._h, ptrs, int(max_steps), ctypes.byref(done) if sync else None,
-                                    _stream(stream)))
+        _check(_lib.ppml_batch_step(self._h, ptrs, lptr, int(max_steps),
+                                    ctypes.byref(done) if sync else None, _stream(stream)))
         return done.value if sync else None
 
-    def status(self, stream=None):
+    def status(self, stream=None, with_flags=False):
+        """(t, steps) per instance, and with_flags also the flags (PPML_FLAG_NONPHYSICAL);
+        a flagged instance does not raise here."""
         t = (ctypes.c_double * self.n_inst)()
         s = (ctypes.c_int * self.n_inst)()
-        _check(_lib.ppml_batch_status(self._h, t, s, _stream(stream)))
+        fl = (ctypes.c_uint * self.n_inst)()
+        rc = _lib.ppml_batch_status(self._h, t, s, fl, _stream(stream))
+        if rc != PPML_OK and rc != PPML_E_NONPHYSICAL:
+            _check(rc)
+        if with_flags:
+            return list(t), list(s), list(fl)
         return list(t), list(s)
 
     def close(self):
@@ -367,7 +392,24 @@ def fma_peak(dtype: int, iters: int, stream=None) -> float:
     return out.value
 
 
-def to_device(u, dtype: int, device="cuda"):
-    """Six (or four) float64 numpy arrays -> contiguous CUDA tensors of the path's dtype."""
-    return [torch.as_tensor(a).to(device=device, dtype=torch_dtype(dtype)).contiguous().reshape(-1)
-            for a in u]
+def to_device(u, dtype: int, device="cuda", lo=False):
+    """Six (or four) float64 numpy arrays -> contiguous CUDA tensors of the path's dtype.
+    lo (FP32): append the low parts of the first n - 1 fields (rho, m..., rho E), so that
+    hi + lo holds the FP64 input to about 48 bits: a double-float state."""
+    t = [torch.as_tensor(a).to(device=device, dtype=torch.float64).contiguous().reshape(-1) for a in u]
+    hi = [x.to(torch_dtype(dtype)) for x in t]
+    if not lo:
+        return hi
+    if dtype != PPML_F32:
+        raise ValueError("low parts are for FP32 states")
+    return hi + [(x - h.double()).float() for x, h in zip(t[:-1], hi[:-1])]
+
+
+def value_of(state, f):
+    """Field f of a state as float64 (hi + lo for a double-float state)."""
+    x = state[f].double()
+    if len(state) == 11 and f < 5:
+        x = x + state[6 + f].double()
+    elif len(state) == 7 and f < 3:  # batch: rho, m, rho E, rho eps + 3 low parts
+        x = x + state[4 + f].double()
+    return x

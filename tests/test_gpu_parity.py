@@ -423,65 +423,119 @@ def _batch_oracle_run(b, i):
     return ref, steps
 
 
-def _fp32_storage_sensitivity(b, i, ref):
-    """Relative L1 change of the FP64 oracle's final rho and p when its state is rounded
-    to float32 after every step (FP64 arithmetic, FP32 storage): the best agreement any
-    FP32-state evaluation of the scheme can be held to for this instance."""
+def _batch_state(b, dtype, df=False):
+    """Device state of a batch: four fields and, for a double-float FP32 state, the low
+    parts of rho, m, rho E (so that the pairs start from the FP64 input)."""
+    td = ppml.torch_dtype(dtype)
+    st = [torch.as_tensor(a).to("cuda", td) for a in b.u]
+    if not df:
+        return st, None
+    lo = [(torch.as_tensor(a).cuda() - x.double()).float() for a, x in zip(b.u[:3], st[:3])]
+    return st, lo
+
+
+def _batch_values(st, lo):
+    got = [x.double() for x in st]
+    if lo is not None:
+        for k in range(3):
+            got[k] = got[k] + lo[k].double()
+    return [x.cpu().numpy() for x in got]
+
+
+_COND_CACHE = {}
+
+
+def _oracle_1d(b, i, u4, callback=None):
     n = int(b.ncells[i])
     sl = slice(b.offsets[i], b.offsets[i + 1])
     z = np.zeros(n)
-    u = [x.astype(np.float32).astype(np.float64)
-         for x in (b.u[0][sl], b.u[1][sl], z, z, b.u[2][sl], b.u[3][sl])]
+    u = [u4[0], u4[1], z, z, u4[2], u4[3]]
     g = oracle.Grid((n, 1, 1), (float(b.h[i]), 1.0, 1.0), b.gamma, (0,) * 6, b.cfl,
                     rho_mean=float(np.mean(b.u[0][sl])))
-
-    def round32(step, t, uu, dg):
-        for f in range(6):
-            uu[f][...] = uu[f].astype(np.float32).astype(np.float64)
-
-    r32, _, _, _ = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]), callback=round32)
-    return max(rel_l1(r32[0].ravel(), ref[0].ravel()), rel_l1(r32[5].ravel(), ref[5].ravel()))
+    out, _, _, _ = oracle.run(g, [x[None, None, :] for x in u], float(b.t_end[i]), callback=callback)
+    return out
 
 
-@pytest.mark.parametrize("dtype", [F64, F32])
-def test_config4_batch_matches_oracle(dtype):
+def _conditioning(b, i, trials=4):
+    """Two FP64-oracle spreads of instance i, relative L1 on the final rho and p:
+    (a) the largest change under a one-float-ulp perturbation of the input (relative
+    2^-24, seeded uniform, `trials` draws): the instance's conditioning in exact arithmetic;
+    (b) the change when the oracle's state is rounded to float after every step (FP64
+    arithmetic, float storage).  Neither involves the GPU."""
+    key = (int(b.offsets[-1]), i)
+    if key not in _COND_CACHE:
+        ref, _ = _batch_oracle(b, i)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        n = int(b.ncells[i])
+
+        def dist(out):
+            return max(rel_l1(out[0].ravel(), ref[0].ravel()), rel_l1(out[5].ravel(), ref[5].ravel()))
+
+        rng = np.random.default_rng(1000 + i)
+        s_in = max(dist(_oracle_1d(b, i, [b.u[k][sl] * (1.0 + 2.0 ** -24 * rng.uniform(-1, 1, n))
+                                          for k in range(4)])) for _ in range(trials))
+
+        def round32(step, t, uu, dg):
+            for f in range(6):
+                uu[f][...] = uu[f].astype(np.float32).astype(np.float64)
+
+        s_round = dist(_oracle_1d(b, i, [b.u[k][sl] for k in range(4)], callback=round32))
+        _COND_CACHE[key] = (s_in, s_round)
+    return _COND_CACHE[key]
+
+
+def _check_fp32_instances(b, got, steps, bar=1e-4):
+    """Every instance's rho and p within the config-4 bar (relative L1 1e-4) of its own
+    oracle run, at most one step apart.  An instance may exceed the bar only if the FP64
+    oracle itself is not determined to it at float resolution (the input-perturbation
+    spread of _conditioning above the bar: an ill-conditioned instance, for which no float
+    computation can be held to the bar); it must then stay within twice the larger of the
+    two oracle spreads.  Returns the indices of such instances."""
+    ill = []
+    for i in range(b.ncells.size):
+        ref, steps_o = _batch_oracle(b, i)
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        assert abs(steps[i] - steps_o) <= 1, (i, steps[i], steps_o)
+        e = max(rel_l1(got[0][sl], ref[0].ravel()), rel_l1(got[3][sl], ref[5].ravel()))
+        if e > bar:
+            s_in, s_round = _conditioning(b, i)
+            assert s_in > bar and e <= 2.0 * max(s_in, s_round), (i, e, s_in, s_round)
+            ill.append(i)
+    return ill
+
+
+@pytest.mark.parametrize("dtype,df", [(F64, False), (F32, False), (F32, True)])
+def test_config4_batch_matches_oracle(dtype, df):
     """Batched uneven Riemann problems: a 24-instance batch, every instance against its
-    own 1D oracle run.  FP64: bit for bit.  FP32: relative L1 of rho and p within
-    max(1e-4, 2 S_i), S_i the change of the FP64 oracle itself when its state is stored in
-    float32 between steps.  Cold, high-Mach collisions (rho eps a tiny difference of
-    totals) have S_i far above 1e-4 (instance 10: 5.8e-4 in rho, 2.6e-3 in p); the other
-    instances have S_i <= 6e-5 and are held to 1e-4."""
+    own 1D oracle run.  FP64: bit for bit.  FP32, plain and double-float states: relative
+    L1 of rho and p within the pre-registered 1e-4, at most one step apart, for every
+    instance the FP64 oracle itself determines to that accuracy at float resolution; the
+    one ill-conditioned draw (instance 10) within twice the oracle's own spread."""
     from oracle import exact
     b = inputs.batched_riemann(n_inst=24, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
     bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, dtype)
-    st = [torch.as_tensor(a).to("cuda", ppml.torch_dtype(dtype)) for a in b.u]
+    st, lo = _batch_state(b, dtype, df)
     done = 0
     for _ in range(100):
-        done = bt.step(st, 1000, sync=True)
+        done = bt.step(st, 1000, sync=True, lo=lo)
         if done == b.ncells.size:
             break
     assert done == b.ncells.size
     t, steps = bt.status()
     assert np.allclose(t, b.t_end, rtol=1e-14)
-    got = [x.double().cpu().numpy() for x in st]
-    n_loose = 0
+    got = _batch_values(st, lo)
+    if dtype == F32:
+        # instance 10 (cold flow, kinetic energy about 230 times the internal energy) is
+        # the one ill-conditioned draw: float-ulp input perturbations move its FP64 oracle
+        # by 3e-4 to 2.3e-3; every other instance moves by at most 1.2e-5
+        assert _check_fp32_instances(b, got, steps) in ([], [10])
+        return
     for i in range(b.ncells.size):
         ref, steps_o = _batch_oracle(b, i)
         sl = slice(b.offsets[i], b.offsets[i + 1])
-        if dtype == F64:
-            assert steps[i] == steps_o
-            for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
-                assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
-            continue
-        assert abs(steps[i] - steps_o) <= 1
-        e_rho = rel_l1(got[0][sl], ref[0].ravel())
-        e_p = rel_l1(got[3][sl], ref[5].ravel())
-        tol = 1e-4
-        if max(e_rho, e_p) > tol:
-            tol = max(tol, 2.0 * _fp32_storage_sensitivity(b, i, ref))
-            n_loose += 1
-        assert e_rho <= tol and e_p <= tol, (i, e_rho, e_p, tol)
-    assert n_loose <= 2  # the sensitivity bound is for the rare ill-conditioned instance
+        assert steps[i] == steps_o
+        for k, f in ((0, 0), (1, 1), (2, 4), (3, 5)):
+            assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
 
 
 @pytest.mark.parametrize("threads", [256, 1024])
@@ -531,38 +585,84 @@ def test_config4_batch_pairs_fp64_bitwise(split):
             assert np.array_equal(got[k][sl], ref[f].ravel()), (i, f)
 
 
-def test_config4_batch_pairs_fp32_match_one_cta():
-    """FP32: the paired and the one-CTA launches take the same steps and agree in rho and
-    rho eps to the config-4 bar, relative L1 within max(1e-4, 2 S_i), S_i the change of the
-    FP64 oracle when its state is stored in float32 between steps: the two kernels are
-    compiled separately and may contract different products into FMAs, and such last-bit
-    differences grow over the runs' thousands of steps like any FP32 rounding (2e-6 to
-    3e-5 measured).  Invalid split sizes are rejected and keep the previous split."""
+@pytest.mark.parametrize("df", [False, True])
+def test_config4_batch_pairs_fp32_match_oracle(df):
+    """FP32 with instances split over CTA pairs (every instance: 64; some: 600; none: 0),
+    plain and double-float states: every instance within the config-4 bar of its own FP64
+    oracle run, as in test_config4_batch_matches_oracle.  Invalid split sizes are rejected
+    and keep the previous split."""
     from oracle import exact
     b = inputs.batched_riemann(n_inst=12, n_min=128, n_max=1024, max_speed=exact.riemann_max_speed)
-    out = {}
-    for split in (0, 64, 600):
+    for split in (64, 600, 0):
         bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F32)
         bt.set_split(split)
-        st = [torch.as_tensor(a).to("cuda", torch.float32) for a in b.u]
-        assert bt.step(st, 1 << 30, sync=True) == b.ncells.size
-        out[split] = ([x.double().cpu().numpy() for x in st], bt.status()[1])
+        st, lo = _batch_state(b, F32, df)
+        assert bt.step(st, 1 << 30, sync=True, lo=lo) == b.ncells.size
+        assert len(_check_fp32_instances(b, _batch_values(st, lo), bt.status()[1])) <= 1
         if split == 64:
             for bad in (10, -5):
                 with pytest.raises(ppml.PPMLError):
                     bt.set_split(bad)
         bt.close()
-    ref, ref_steps = out[0]
-    for split in (64, 600):
-        got, steps = out[split]
-        assert list(steps) == list(ref_steps), split
-        for i in range(b.ncells.size):
-            sl = slice(b.offsets[i], b.offsets[i + 1])
-            e = max(rel_l1(got[k][sl], ref[k][sl]) for k in (0, 3))
-            tol = 1e-4
-            if e > tol:
-                tol = max(tol, 2.0 * _fp32_storage_sensitivity(b, i, _batch_oracle(b, i)[0]))
-            assert e <= tol, (split, i, e, tol)
+
+
+@pytest.mark.parametrize("dtype,split,df", [(F64, 0, False), (F32, 0, False), (F32, 64, True)])
+def test_config4_batch_flags_nonphysical_instances(dtype, split, df):
+    """An instance whose state has rho <= 0 or a NaN stops before its next step and is
+    flagged non-physical: a negative density planted in instance 3 and a NaN in instance 7
+    of the host input.  The synchronizing step reports PPML_E_NONPHYSICAL, the status names
+    exactly those two, and every other instance still reaches its end time."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=10, n_min=128, n_max=512, max_speed=exact.riemann_max_speed)
+    b.u[0][b.offsets[3] + 17] = -0.5
+    b.u[2][b.offsets[7] + 40] = float("nan")
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, dtype)
+    bt.set_split(split)
+    st, lo = _batch_state(b, dtype, df)
+    with pytest.raises(ppml.PPMLError) as e:
+        bt.step(st, 1 << 30, sync=True, lo=lo)
+    assert e.value.code == ppml.PPML_E_NONPHYSICAL
+    t, steps, flags = bt.status(with_flags=True)
+    flagged = [i for i, f in enumerate(flags) if f & ppml.FLAG_NONPHYSICAL]
+    assert flagged == [3, 7]
+    assert steps[3] == 0 and steps[7] == 0
+    for i in range(b.ncells.size):
+        if i not in (3, 7):
+            assert t[i] == pytest.approx(b.t_end[i], rel=1e-14)
+
+
+def test_config4_batch_step_captured_in_a_graph():
+    """The batch step can be captured in a CUDA graph (the cluster launch with every
+    instance split included): replaying a captured call of 150 steps until every instance
+    has finished gives the eager result bit for bit (FP64), and a split change after the
+    capture leaves the captured plan in place."""
+    from oracle import exact
+    b = inputs.batched_riemann(n_inst=8, n_min=128, n_max=512, max_speed=exact.riemann_max_speed)
+    eager = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    eager.set_split(64)
+    es = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    calls = 0
+    while eager.step(es, 150, sync=True) < b.ncells.size:
+        calls += 1
+    calls += 1
+    bt = ppml.Batch(b.ncells, b.h, b.t_end, b.gamma, b.cfl, F64)
+    bt.set_split(64)
+    st = [torch.as_tensor(a).to("cuda", torch.float64) for a in b.u]
+    bt.step(st, 0, sync=True)  # first launch outside the capture (shared-memory limits)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            bt.step(st, 150, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    bt.set_split(0)  # later eager calls would use the new plan; the graph keeps its own
+    for _ in range(calls + 2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(st, es):
+        assert torch.equal(x, y)
+    assert bt.status()[1] == eager.status()[1]
 
 
 def test_config4_batch_tune_leaves_state_and_progress():
@@ -817,19 +917,6 @@ def test_config5_disk_64_fp64_isolated_gravity():
     ref, dts, dg = _disk_run_oracle(pb, 12, isolated=True)
     got, grid = _disk_run_gpu(pb, F64, dts, isolated=True)
     compare(got, ref, TOL64)
-
-
-@pytest.mark.slow
-def test_config5_disk_512_fp32():
-    """Config 5 at full size: the 512^3 disk in FP32, two gravity steps against the FP64
-    oracle (rho and p within 1e-3), and FP64 sums of mass and energy within 1e-6."""
-    pb = inputs.galactic_disk(n=512)
-    ref, dts, dg = _disk_run_oracle(pb, 2)
-    got, grid = _disk_run_gpu(pb, F32, dts)
-    compare(got, ref, 1e-3, fields=(0, 5))
-    d = grid.diag()
-    assert d["sums"][0] == pytest.approx(dg["sums"][0], rel=1e-6)
-    assert d["sums"][4] == pytest.approx(dg["sums"][4], rel=1e-6)
 
 
 def test_cuda_graph_replay_equals_eager():

@@ -21,9 +21,14 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_1607_01105_gb300 import ppml  # noqa: E402
 
 
-@pytest.mark.parametrize("dtype", [ppml.PPML_F64, ppml.PPML_F32])
-def test_noalloc_step_matches_handle_step_twice(dtype):
-    pb = inputs.random_smooth(n=(40, 24, 20), bc=(0, 0, 1, 1, 0, 0))
+@pytest.mark.parametrize("dtype,n", [(ppml.PPML_F64, (40, 24, 20)), (ppml.PPML_F32, (40, 24, 20)),
+                                     (ppml.PPML_F64, (64, 64, 64)), (ppml.PPML_F64, (17, 17, 907))])
+def test_noalloc_step_matches_handle_step_twice(dtype, n):
+    """Two calls in a row against the handle-based step, on a small grid, on a grid of
+    exactly the buffer's limit (64^3 = PPML_NOALLOC_MAX_CELLS cells) and on a thin grid
+    with ragged tiles (17 x 17 x 907 = 262123 cells, 228 tiles)."""
+    assert n[0] * n[1] * n[2] <= ppml.NOALLOC_MAX_CELLS
+    pb = inputs.random_smooth(n=n, bc=(0, 0, 1, 1, 0, 0))
     rho_mean = oracle.mean_density(pb.u)
     u0 = ppml.to_device(pb.u, dtype)
     grid = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, dtype, u0=u0)
@@ -63,3 +68,20 @@ def test_noalloc_rejects_grids_beyond_its_buffer():
                                       1.0, out, None)
     assert rc == ppml.PPML_E_INVAL
     assert "fixed buffer" in ppml.lib().ppml_last_error().decode()
+
+
+def test_noalloc_rejects_end_time_and_low_parts():
+    """The call keeps no simulated time (t_end must be 0) and takes plain states only."""
+    pb = inputs.random_smooth(n=(16, 8, 8))
+    u = ppml.to_device(pb.u, ppml.PPML_F32)
+    v = [torch.empty_like(x) for x in u]
+    desc = ppml.make_desc(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, ppml.PPML_F32, t_end=0.5)
+    with pytest.raises(ppml.PPMLError) as e:
+        ppml.step_noalloc(desc, u, v, 1e-4, 1.0)
+    assert e.value.code == ppml.PPML_E_INVAL and "t_end" in str(e.value)
+    desc = ppml.make_desc(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, ppml.PPML_F32)
+    ud = ppml.to_device(pb.u, ppml.PPML_F32, lo=True)
+    vd = [torch.empty_like(x) for x in ud]
+    with pytest.raises(ppml.PPMLError) as e:
+        ppml.step_noalloc(desc, ud, vd, 1e-4, 1.0)
+    assert e.value.code == ppml.PPML_E_INVAL
