@@ -190,6 +190,23 @@ int ppml_fourier_amplitudes(ppml_grid* g, const void* rho, double r_f, int m_max
 int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, double G, unsigned flags,
                           void* stream);
 
+/* Launch shape of the stage kernels (the paper has no counterpart: a systems choice).  A
+ * step runs one CTA per 16^3 tile; the tiles are launched in one of PPML_TILE_ORDERS
+ * orders, which decide which tiles run at the same time and hence which halos and template
+ * boxes the L2 cache still holds: 0 x-major (ppml_init_grid's choice), 1 z-major, 2 in
+ * blocks of 2^3 tiles, 3 in blocks of 4^3 tiles (x-major within and over the blocks).
+ * Results do not depend on the order (every tile computes the same values, and the CFL and
+ * sum partials are reduced in tile order).  ppml_grid_set_order fixes it (PPML_E_INVAL for
+ * another value).  ppml_grid_tune times each order for trial_steps (>= 1) steps, the faster
+ * of two runs, on scratch copies of u's six fields with the handle's step scalars saved
+ * and restored (u and the handle's time are unchanged), keeps the fastest and returns it
+ * in *order_out (may be NULL) and the times in ms_out (may be NULL).  It allocates and
+ * frees two scratch states and synchronizes the stream; do not capture it in a graph. */
+#define PPML_TILE_ORDERS 4
+int ppml_grid_set_order(ppml_grid* g, int order);
+int ppml_grid_tune(ppml_grid* g, const ppml_state* u, int trial_steps, int* order_out,
+                   double ms_out[PPML_TILE_ORDERS], void* stream);
+
 /* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated; with
  * their low parts for double-float states) into u_star.  For stage-level checks; same dt
  * convention as ppml_step; does not advance t. */

@@ -37,8 +37,9 @@ struct MarchArgs {
   double dt_host;        // used when dt_dev == NULL
   const double* dt_dev;  // device-resident step
   double rho_vac;
-  Partial* partials;
-  int tiles_x, tiles_y;  // tile grid of the stage kernels (z tiles = grid / (x * y))
+  Partial* partials;      // per tile of the Lagrangian stage, at the tile's x-major index
+  int tiles_x, tiles_y, tiles_z;  // tile grid of the stage kernels
+  int tile_order;         // launch order of the tiles (TileOrder)
   int any_reflect;       // a reflecting wall exists (its sign flips need register copies)
   int flags;             // PPML_FIRST_ORDER, PPML_VHAT_1PT
 };
@@ -66,10 +67,12 @@ __device__ __forceinline__ void cta_step_constants(const double* dt_dev, double 
 
 // ------------------------------------------------------------------ block reduction
 
+// Writes the CTA's partial to out[slot].
 template <int NTHREADS>
 __device__ __forceinline__ void block_reduce_store(double s[6], double vmax, double cmax,
                                                    unsigned long long nvac,
-                                                   unsigned long long nbad, Partial* out) {
+                                                   unsigned long long nbad, Partial* out,
+                                                   int slot) {
   __shared__ double sh[NTHREADS / 32][8];
   __shared__ unsigned long long shc[NTHREADS / 32][2];
 #pragma unroll
@@ -104,7 +107,7 @@ __device__ __forceinline__ void block_reduce_store(double s[6], double vmax, dou
       p.nvac += shc[q][0];
       p.nbad += shc[q][1];
     }
-    out[blockIdx.x] = p;
+    out[slot] = p;
   }
 }
 
@@ -123,7 +126,7 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl)
 template <int NTHREADS>
 __device__ __forceinline__ void block_reduce_store_f32(const float hi_in[6], const float lo_in[6],
                                                        float vmax, float cmax, unsigned nvac,
-                                                       unsigned nbad, Partial* out) {
+                                                       unsigned nbad, Partial* out, int slot) {
   float hi[6], lo[6];
 #pragma unroll
   for (int f = 0; f < 6; f++) {
@@ -168,7 +171,7 @@ __device__ __forceinline__ void block_reduce_store_f32(const float hi_in[6], con
       p.nvac += shc[q][0];
       p.nbad += shc[q][1];
     }
-    out[blockIdx.x] = p;
+    out[slot] = p;
   }
 }
 
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(NT) diag_kernel(MarchArgs<T> A) {
   }
   double sd[6];
   sums.get(sd);
-  block_reduce_store<NT>(sd, (double)vmax, (double)cmax, 0ull, nbad, A.partials);
+  block_reduce_store<NT>(sd, (double)vmax, (double)cmax, 0ull, nbad, A.partials, blockIdx.x);
 }
 
 }  // namespace ppml

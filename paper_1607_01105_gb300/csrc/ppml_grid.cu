@@ -109,8 +109,10 @@ struct ppml_grid {
   void* ustar[6];  // [0] unused (rho is not changed by the Eulerian stage)
   void* ustar_lo[5];  // FP32: low parts of U*'s m and rho E ([0] unused)
   Partial* partials;
-  int nblk_march, nblk_diag, npartials;
+  int nblk_march, nblk_diag, npartials;  // tiles (partials of a step), diagnostics blocks
   int tiles_x, tiles_y, tiles_z;
+  int tile_order;   // launch order of the stage kernels' tiles (ppml_grid_tune)
+  int nblk_launch;  // blocks of a stage launch in that order
   DevScalars* dev;
   double rho_mean, rho_vac, hmin, vol;
   // measurement hook: events around each kernel of a step
@@ -207,6 +209,8 @@ MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev)
   A.partials = g->partials;
   A.tiles_x = g->tiles_x;
   A.tiles_y = g->tiles_y;
+  A.tiles_z = g->tiles_z;
+  A.tile_order = g->tile_order;
   A.any_reflect = 0;
   for (int q = 0; q < 6; q++) A.any_reflect |= g->d.bc[q] == PPML_BC_REFLECT;
   A.flags = g->d.flags;
@@ -238,7 +242,7 @@ int run_eulerian(ppml_grid* g, const ppml_state* u, void* const out[6], void* co
       A.outlo[f] = (T*)outlo[f];
     }
   A.phi = phi;
-  return launch_eulerian<T>(A, g->nblk_march, st);
+  return launch_eulerian<T>(A, g->nblk_launch, st);
 }
 
 // Fold the recorded events of finished steps into the per-kernel totals.
@@ -285,7 +289,7 @@ int run_step(ppml_grid* g, const ppml_state* uin, ppml_state* uout, const T* phi
     for (int f = 1; f < 5; f++) L.ulo[f] = (const T*)g->ustar_lo[f];
     for (int f = 0; f < 5; f++) L.outlo[f] = (T*)uout->lo[f];
   }
-  rc = launch_lagrangian<T>(L, g->nblk_march, st);
+  rc = launch_lagrangian<T>(L, g->nblk_launch, st);
   if (rc) return rc;
   if (ev) cudaEventRecord(ev[2], st);
   rc = launch_finalize(g->partials, g->nblk_march, g->dev, g->d.cfl, g->hmin, g->vol,
@@ -322,6 +326,8 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
   g->tiles_y = (d->ny + TB - 1) / TB;
   g->tiles_z = (d->nz + TB - 1) / TB;
   g->nblk_march = g->tiles_x * g->tiles_y * g->tiles_z;
+  g->tile_order = 0;
+  g->nblk_launch = g->nblk_march;
   g->nblk_diag = (int)std::min<long long>((g->geom.ncell + NT - 1) / NT, 4 * 152);
   g->npartials = std::max(g->nblk_march, g->nblk_diag);
   g->hmin = INFINITY;
@@ -646,5 +652,95 @@ extern "C" int ppml_kernel_times(ppml_grid* g, double ms[3], long long* steps) {
   if (rc) return rc;
   for (int q = 0; q < 3; q++) ms[q] = g->ms[q];
   if (steps) *steps = g->prof_steps;
+  return PPML_OK;
+}
+
+extern "C" int ppml_grid_set_order(ppml_grid* g, int order) {
+  ppml_clear_error();
+  if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
+  if (order < 0 || order >= kTileOrders)
+    return ppml_fail(PPML_E_INVAL, "tile order %d not in [0, %d)", order, kTileOrders);
+  const long long nb = order_blocks(order, g->tiles_x, g->tiles_y, g->tiles_z);
+  if (nb > (1ll << 31) - 1) return ppml_fail(PPML_E_INVAL, "too many blocks for order %d", order);
+  g->tile_order = order;
+  g->nblk_launch = (int)nb;
+  return PPML_OK;
+}
+
+extern "C" int ppml_grid_tune(ppml_grid* g, const ppml_state* u, int trial_steps, int* order_out,
+                              double ms_out[PPML_TILE_ORDERS], void* stream) {
+  ppml_clear_error();
+  if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
+  int rc = ppml_validate_state(u, "u");
+  if (rc) return rc;
+  rc = check_state_type(&g->d, u, "u");
+  if (rc) return rc;
+  if (trial_steps < 1) return ppml_fail(PPML_E_INVAL, "trial_steps = %d must be >= 1", trial_steps);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t fbytes = (size_t)g->geom.ncell * g->elt;
+  // two scratch states (the trials ping-pong between them from a copy of u's fields) and
+  // the handle's step scalars, restored at the end
+  void* buf[12] = {};
+  DevScalars keep;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int prof = g->profiling, order0 = g->tile_order;
+  g->profiling = 0;
+  for (int q = 0; q < 12 && rc == PPML_OK; q++)
+    if (cudaMalloc(&buf[q], fbytes) != cudaSuccess) rc = ppml_fail(PPML_E_NOMEM, "tuning scratch state");
+  if (rc == PPML_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = ppml_fail(PPML_E_CUDA, "cudaEventCreate failed");
+  if (rc == PPML_OK && (cudaMemcpyAsync(&keep, g->dev, sizeof(keep), cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+    rc = ppml_fail(PPML_E_CUDA, "tuning: %s", cudaGetErrorString(cudaGetLastError()));
+  ppml_state sa = {}, sb = {};
+  for (int f = 0; f < 6; f++) {
+    sa.f[f] = buf[f];
+    sb.f[f] = buf[6 + f];
+  }
+  double best_ms = 0.0;
+  int best = order0;
+  for (int order = 0; order < kTileOrders && rc == PPML_OK; order++) {
+    rc = ppml_grid_set_order(g, order);
+    float best_k = 0.f;
+    for (int rep = 0; rep < 2 && rc == PPML_OK; rep++) {  // the first repetition also warms up
+      for (int f = 0; f < 6 && rc == PPML_OK; f++)
+        if (cudaMemcpyAsync(sa.f[f], u->f[f], fbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          rc = ppml_fail(PPML_E_CUDA, "tuning copy: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rc == PPML_OK && cudaMemcpyAsync(g->dev, &keep, sizeof(keep), cudaMemcpyHostToDevice, st) !=
+                               cudaSuccess)
+        rc = ppml_fail(PPML_E_CUDA, "tuning copy: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < trial_steps && rc == PPML_OK; k++)
+        rc = g->d.dtype == PPML_F64
+                 ? run_step<double>(g, k % 2 ? &sb : &sa, k % 2 ? &sa : &sb, nullptr, 0.0, &g->dev->dt, st)
+                 : run_step<float>(g, k % 2 ? &sb : &sa, k % 2 ? &sa : &sb, nullptr, 0.0, &g->dev->dt, st);
+      if (rc) break;
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = ppml_fail(PPML_E_CUDA, "tuning timing: %s", cudaGetErrorString(cudaGetLastError()));
+      if (rep == 0 || ms < best_k) best_k = ms;
+    }
+    if (rc) break;
+    if (ms_out) ms_out[order] = best_k;
+    if (order == 0 || best_k < best_ms) {
+      best_ms = best_k;
+      best = order;
+    }
+  }
+  if (rc == PPML_OK &&
+      (cudaMemcpyAsync(g->dev, &keep, sizeof(keep), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = ppml_fail(PPML_E_CUDA, "tuning restore: %s", cudaGetErrorString(cudaGetLastError()));
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int q = 0; q < 12; q++)
+    if (buf[q]) cudaFree(buf[q]);
+  g->profiling = prof;
+  ppml_grid_set_order(g, rc == PPML_OK ? best : order0);
+  if (rc) return rc;
+  if (order_out) *order_out = best;
   return PPML_OK;
 }

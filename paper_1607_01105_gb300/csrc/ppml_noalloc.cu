@@ -88,6 +88,8 @@ int step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in, ppml_state* u_
   A.tiles_x = (d->nx + TB - 1) / TB;
   A.tiles_y = (d->ny + TB - 1) / TB;
   const int tiles_z = (d->nz + TB - 1) / TB;
+  A.tiles_z = tiles_z;
+  A.tile_order = 0;
   const int nblk = A.tiles_x * A.tiles_y * tiles_z;
   if ((size_t)nblk > kMaxPartials)
     return ppml_fail(PPML_E_INVAL, "grid needs %d tiles (the fixed buffer holds %zu)", nblk,

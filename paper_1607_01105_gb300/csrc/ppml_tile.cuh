@@ -35,16 +35,69 @@ __device__ __forceinline__ int acc_at(int i, int j, int k) { return i + ARP * j 
 
 struct TileGeom {
   int i0, j0, k0;
-  bool fast;  // every cell within 3 of the tile is inside the domain on active axes
+  int id;      // x-major index of the tile (its slot in the per-tile partials)
+  bool valid;  // false for the padding blocks of a blocked order (no tile)
+  bool fast;   // every cell within 3 of the tile is inside the domain on active axes
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, int tiles_x, int tiles_y) {
+// Launch orders of the tiles (a systems choice, not the paper's: which tiles run
+// concurrently, hence which halos the L2 holds).  Each tile computes the same values in any
+// order, and the partials go to the tile's own slot.
+//   0 x-major: x tile index fastest, then y, then z
+//   1 z-major: z fastest, then y, then x
+//   2, 3 blocked: blocks of 2^3 (4^3) tiles (fewer along axes with fewer tiles), x-major
+//     within a block and over the blocks; blocks past the grid's edge are empty
+constexpr int kTileOrders = 4;
+static_assert(kTileOrders == PPML_TILE_ORDERS, "tile orders of the C ABI");
+
+__host__ __device__ __forceinline__ int order_block(int order, int tiles) {
+  const int s = order == 2 ? 2 : (order == 3 ? 4 : 1);
+  return s < tiles ? s : tiles;
+}
+
+// Blocks launched for a tile grid in an order (the tile count, or more for padded blocks).
+__host__ __device__ __forceinline__ long long order_blocks(int order, int tx, int ty, int tz) {
+  const int sx = order_block(order, tx), sy = order_block(order, ty), sz = order_block(order, tz);
+  return (long long)((tx + sx - 1) / sx * sx) * ((ty + sy - 1) / sy * sy) * ((tz + sz - 1) / sz * sz);
+}
+
+__device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, const int tiles[3], int order) {
   TileGeom t;
   int b = blockIdx.x;
-  t.i0 = (b % tiles_x) * TB;
-  b /= tiles_x;
-  t.j0 = (b % tiles_y) * TB;
-  t.k0 = (b / tiles_y) * TB;
+  int tc[3];
+  if (order == 1) {
+    tc[2] = b % tiles[2];
+    b /= tiles[2];
+    tc[1] = b % tiles[1];
+    tc[0] = b / tiles[1];
+  } else if (order >= 2) {
+    int s[3], nsup[3];
+    for (int a = 0; a < 3; a++) {
+      s[a] = order_block(order, tiles[a]);
+      nsup[a] = (tiles[a] + s[a] - 1) / s[a];
+    }
+    const int per = s[0] * s[1] * s[2];
+    int sup = b / per, r = b % per;
+    const int l0 = r % s[0];
+    r /= s[0];
+    const int l1 = r % s[1], l2 = r / s[1];
+    const int S0 = sup % nsup[0];
+    sup /= nsup[0];
+    const int S1 = sup % nsup[1], S2 = sup / nsup[1];
+    tc[0] = S0 * s[0] + l0;
+    tc[1] = S1 * s[1] + l1;
+    tc[2] = S2 * s[2] + l2;
+  } else {
+    tc[0] = b % tiles[0];
+    b /= tiles[0];
+    tc[1] = b % tiles[1];
+    tc[2] = b / tiles[1];
+  }
+  t.valid = tc[0] < tiles[0] && tc[1] < tiles[1] && tc[2] < tiles[2];
+  t.id = tc[0] + tiles[0] * (tc[1] + tiles[1] * tc[2]);
+  t.i0 = tc[0] * TB;
+  t.j0 = tc[1] * TB;
+  t.k0 = tc[2] * TB;
   const int o[3] = {t.i0, t.j0, t.k0};
   bool f = true;
   for (int a = 0; a < 3; a++) f = f && g.n[a] > 1 && o[a] - TH >= 0 && o[a] + TB + TH <= g.n[a];
@@ -422,7 +475,9 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   const GridGeom& g = A.g;
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
-  const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const int tiles[3] = {A.tiles_x, A.tiles_y, A.tiles_z};
+  const TileGeom tg = tile_geom(g, tiles, A.tile_order);
+  if (!tg.valid) return;  // a padding block of a blocked order (uniform over the CTA)
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   const bool fast_async = async_ok && tg.fast;
   T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
@@ -720,11 +775,12 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       hi[f] = sums.s[f].hi;
       lo[f] = sums.s[f].lo;
     }
-    block_reduce_store_f32<TN>(hi, lo, vmax, cmax, (unsigned)nvac, (unsigned)nbad, A.partials);
+    block_reduce_store_f32<TN>(hi, lo, vmax, cmax, (unsigned)nvac, (unsigned)nbad, A.partials,
+                               tg.id);
   } else {
     double sd[6];
     sums.get(sd);
-    block_reduce_store<TN>(sd, (double)vmax, (double)cmax, nvac, nbad, A.partials);
+    block_reduce_store<TN>(sd, (double)vmax, (double)cmax, nvac, nbad, A.partials, tg.id);
   }
 }
 
@@ -750,7 +806,9 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const GridGeom& g = A.g;
   const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
   const int tid = threadIdx.x, a = tid % TB, b = tid / TB;
-  const TileGeom tg = tile_geom(g, A.tiles_x, A.tiles_y);
+  const int tiles[3] = {A.tiles_x, A.tiles_y, A.tiles_z};
+  const TileGeom tg = tile_geom(g, tiles, A.tile_order);
+  if (!tg.valid) return;  // a padding block of a blocked order (uniform over the CTA)
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   __shared__ TileMaps maps;
   build_maps(maps, g, tg);  // ordered by the barrier below

@@ -30,7 +30,8 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
             "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak",
-            "ppml_batch_set_split", "ppml_batch_plan")
+            "ppml_batch_set_split", "ppml_batch_plan", "ppml_grid_tune", "ppml_grid_set_order")
+TILE_ORDERS = 4  # launch orders of the stage kernels' tiles (ppml_grid_tune)
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
 
@@ -89,6 +90,9 @@ _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(Stat
                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.ppml_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.ppml_grid_set_order.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_grid_tune.argtypes = [_vp, ctypes.POINTER(State), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double), _vp]
 
 
 class PPMLError(RuntimeError):
@@ -240,6 +244,20 @@ class Grid:
         return {"t": d.t, "dt_next": d.dt_next, "vmax": d.vmax, "cmax": d.cmax,
                 "sums": list(d.sums), "steps": d.steps, "n_vacuum": d.n_vacuum,
                 "n_bad": d.n_bad, "flags": d.flags}
+
+    def set_order(self, order):
+        """Launch order of the stage kernels' tiles (0 x-major, 1 z-major, 2 and 3 blocked)."""
+        _check(_lib.ppml_grid_set_order(self._h, int(order)))
+
+    def tune(self, u, trial_steps=5, stream=None):
+        """Time each tile order on scratch copies of u's fields; keep the fastest.
+        Returns (order, {order: ms})."""
+        st = _state(u, self.tdtype, self.cells)
+        chosen = ctypes.c_int(-1)
+        ms = (ctypes.c_double * TILE_ORDERS)()
+        _check(_lib.ppml_grid_tune(self._h, ctypes.byref(st), int(trial_steps), ctypes.byref(chosen),
+                                   ms, _stream(stream)))
+        return chosen.value, dict(enumerate(list(ms)))
 
     def dt_device_ptr(self) -> int:
         return _lib.ppml_dt_device(self._h)

@@ -948,6 +948,44 @@ def test_cuda_graph_replay_equals_eager():
     assert gg.diag()["steps"] == 4
 
 
+def test_tile_orders_bitwise_identical_and_tuner():
+    """Every launch order of the stage kernels' tiles (x-major, z-major, blocks of 2^3 and
+    4^3 tiles, padded at the grid's ragged edges) gives the oracle's FP64 state bit for bit
+    over three steps with the device CFL step, and bitwise identical conservation sums.
+    The tuner times the orders on scratch copies: the state and the handle's time are
+    unchanged, the chosen order is the fastest measured and is kept."""
+    pb = inputs.random_rough(n=(37, 29, 21), bc=(2, 0, 1, 1, 0, 2))
+    g = oracle_grid(pb)
+    ref = pb.u
+    for _ in range(3):
+        ref, dgo = oracle.step(g, ref, oracle.cfl_dt(g, ref))
+    sums = []
+    for order in range(ppml.TILE_ORDERS):
+        u = ppml.to_device(pb.u, F64)
+        v = [torch.empty_like(x) for x in u]
+        grid = gpu_grid(pb, F64, u)
+        grid.set_order(order)
+        for _ in range(3):
+            grid.step(u, v, 0.0)
+            u, v = v, u
+        got = host(u, shape_of(pb))
+        assert [int(np.count_nonzero(got[f] != ref[f])) for f in range(6)] == [0] * 6, order
+        sums.append(grid.diag()["sums"])
+        grid.close()
+    assert all(s_ == sums[0] for s_ in sums)
+    u = ppml.to_device(pb.u, F64)
+    before = [x.clone() for x in u]
+    grid = gpu_grid(pb, F64, u)
+    d0 = grid.diag()
+    order, ms = grid.tune(u, trial_steps=2)
+    assert order in range(ppml.TILE_ORDERS) and ms[order] == min(ms.values()) > 0.0
+    assert all(torch.equal(x, y) for x, y in zip(u, before))
+    d1 = grid.diag()
+    assert (d1["t"], d1["steps"], d1["dt_next"]) == (d0["t"], d0["steps"], d0["dt_next"])
+    with pytest.raises(ppml.PPMLError):
+        grid.set_order(ppml.TILE_ORDERS)
+
+
 def test_fma_peak_measurement():
     """The FMA-throughput probe behind the arithmetic rooflines: finite, positive, FP32
     within the range a 152-SM part at up to 2.1 GHz allows (128 FP32 lanes per SM, one FMA
