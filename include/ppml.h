@@ -54,7 +54,12 @@ typedef enum {
   PPML_F64 = 1  /* everything in double */
 } ppml_dtype;
 
-typedef enum { PPML_BC_OUTFLOW = 0, PPML_BC_PERIODIC = 1, PPML_BC_REFLECT = 2 } ppml_bc;
+typedef enum {
+  PPML_BC_OUTFLOW = 0,
+  PPML_BC_PERIODIC = 1,
+  PPML_BC_REFLECT = 2,
+  PPML_BC_HALO = 3 /* z faces only: a slab of a z-decomposed grid (see "z-slab decomposition") */
+} ppml_bc;
 
 /* scheme variants (ppml_grid_desc.flags) */
 #define PPML_FIRST_ORDER 1u /* piecewise-constant states in both stages (Sec. 1.1, the first-order
@@ -80,6 +85,8 @@ typedef struct {
                          <= 0 selects 1e-5 */
   double t_end;       /* > 0: the device-side CFL step is clipped so t lands on t_end */
   int flags;          /* PPML_FIRST_ORDER | PPML_VHAT_1PT variants; 0 = the PPML scheme */
+  double rho_ref;     /* > 0: reference density of the vacuum threshold (a slab passes the
+                         whole grid's mean); 0: the mean of the initial state */
 } ppml_grid_desc;
 
 /* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions), and for FP32
@@ -207,9 +214,49 @@ int ppml_grid_set_order(ppml_grid* g, int order);
 int ppml_grid_tune(ppml_grid* g, const ppml_state* u, int trial_steps, int* order_out,
                    double ms_out[PPML_TILE_ORDERS], void* stream);
 
+/* ------------------------------------------------------------ z-slab decomposition
+ * A grid split along z into slabs, one per GPU (the paper runs on one node and has no
+ * decomposition; this is the timestep spread over devices).  A slab's grid is the grid with
+ * nz = the slab's planes and PPML_BC_HALO on each z face it shares with another slab (the
+ * whole grid's own z boundaries stay on the outer slabs' other faces; a periodic z axis
+ * makes both faces of every slab halo faces).  Behind a halo face the caller's arrays hold
+ * PPML_HALO_PLANES planes of the neighbour's cells: the caller allocates them before
+ * (after) the interior planes and passes pointers to the first interior plane.  That holds
+ * for the state and for the U* arrays given to the stage calls; low parts of double-float
+ * states need no halo planes.  One step of every slab, ranks in lockstep:
+ *   fill U^n's halo planes from the neighbours; ppml_eulerian_stage(g, u, u_star, dt);
+ *   fill u_star's halo planes from the neighbours;
+ *   ppml_lagrangian_stage(g, u_star, u_out, dt, red);
+ *   all-reduce red over the slabs (max of red[0..1], sum of red[2..9]);
+ *   ppml_apply_reduced(g, red, 1, dt).
+ * Before the first step: ppml_local_reduce(g, u0, red), the all-reduce, and
+ * ppml_apply_reduced(g, red, 0, 0) set the first CFL step.  dt > 0: that step for every
+ * call of the step; dt <= 0: the device-resident step.  The states then equal a single grid's
+ * bit for bit (every cell takes the same operations on the same values; the CFL step comes
+ * from the same maxima); the sums differ only in the order of addition.  Grids with halo
+ * faces are refused by ppml_step, ppml_step_phi, ppml_step_noalloc, the Poisson solves and
+ * ppml_grid_tune, which step through the handle's own U* (it has no halo planes).
+ * red: PPML_REDUCE_LEN device doubles, caller-owned: max|v|, max c, the six FP64 sums
+ * (times the cell volume), the counts of vacuum-branch and of non-physical cells.
+ *   ppml_local_reduce      red of the state u's cells (this slab's), asynchronous
+ *   ppml_lagrangian_stage  S5-S8 from the caller's U* (rho in u_star->f[0], as
+ *                          ppml_eulerian_stage writes it) into u_out, and red of u_out;
+ *                          does not advance the handle's time; asynchronous
+ *   ppml_apply_reduced     the handle's scalars (t, steps, maxima, sums, flags, next CFL
+ *                          step) from an all-reduced red; advance != 0 adds the step of
+ *                          size dt (dt <= 0: the device-resident step); asynchronous */
+#define PPML_HALO_PLANES 3
+#define PPML_REDUCE_LEN 10
+int ppml_local_reduce(ppml_grid* g, const ppml_state* u, double* red, void* stream);
+int ppml_lagrangian_stage(ppml_grid* g, const ppml_state* u_star, ppml_state* u_out, double dt,
+                          double* red, void* stream);
+int ppml_apply_reduced(ppml_grid* g, const double* red, int advance, double dt, void* stream);
+
 /* Only the Eulerian stage (S0-S3): writes U* (rho copied, m, rho E, rho eps updated; with
- * their low parts for double-float states) into u_star.  For stage-level checks; same dt
- * convention as ppml_step; does not advance t. */
+ * their low parts for double-float states) into u_star.  The stage does not change rho:
+ * u_star->f[0] (and lo[0]) may be u_in's, and is then left as it is.  Used for stage-level
+ * checks and by the z-slab decomposition; same dt convention as ppml_step; does not
+ * advance t. */
 int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_state* u_star, double dt,
                         void* stream);
 

@@ -80,6 +80,9 @@ def lib():
         _lib.oracle_face_lambda.restype = ctypes.c_double
         _lib.oracle_energy_correction.argtypes = [_dp, ctypes.c_double]
         _lib.oracle_energy_correction.restype = ctypes.c_int
+        _lib.oracle_lagrangian_step.argtypes = [ctypes.POINTER(_Desc), _P6, _P6, ctypes.c_double,
+                                                ctypes.c_double, ctypes.POINTER(Diag)]
+        _lib.oracle_lagrangian_step.restype = ctypes.c_int
         _lib.oracle_face_velocities.argtypes = [ctypes.POINTER(_Desc), _P6, ctypes.c_int, _dp]
         _lib.oracle_face_velocities.restype = ctypes.c_int
     return _lib
@@ -144,6 +147,20 @@ def step(grid: Grid, u, tau: float, phi=None, want_star: bool = False):
         raise MemoryError("oracle_step failed to allocate")
     if want_star:
         return uout, dg.as_dict(), ustar
+    return uout, dg.as_dict()
+
+
+def lagrangian_step(grid: Grid, u_star, tau: float):
+    """The second half of a step (S4-S11) from a given U*: returns (u_next, diag_dict)."""
+    shape = (grid.n[2], grid.n[1], grid.n[0])
+    us = _as_fields(u_star, shape)
+    uout = [np.empty(shape) for _ in range(6)]
+    dg = Diag()
+    d = grid.desc()
+    rc = lib().oracle_lagrangian_step(ctypes.byref(d), _ptrs(us), _ptrs(uout), float(tau),
+                                      float(grid.cfl), ctypes.byref(dg))
+    if rc != 0:
+        raise MemoryError("oracle_lagrangian_step failed to allocate")
     return uout, dg.as_dict()
 
 

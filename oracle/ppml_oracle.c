@@ -649,6 +649,49 @@ int oracle_face_velocities(const oracle_desc* d, double* const u_star[NFIELD], i
   return 0;
 }
 
+/* S4-S11 alone: the Lagrangian stage, the energy correction and the diagnostics of a given
+ * U* (six interior-only arrays, ghost-filled here with the descriptor's boundaries), as the
+ * second half of oracle_step.  Used to check a decomposition of the step over z slabs,
+ * whose U* is exchanged between the stages. */
+int oracle_lagrangian_step(const oracle_desc* d, double* const u_star[NFIELD],
+                           double* const u_out[NFIELD], double tau, double cfl, oracle_diag* diag) {
+  gshape s = make_shape(d);
+  double* Us[NFIELD];
+  double* Un[NFIELD];
+  for (int f = 0; f < NFIELD; f++) {
+    Us[f] = (double*)calloc(s.cells, sizeof(double));
+    Un[f] = (double*)calloc(s.cells, sizeof(double));
+    if (!Us[f] || !Un[f]) return -1;
+    scatter_interior(&s, u_star[f], Us[f]);
+    fill_ghosts(&s, d, Us[f], f); /* S4 */
+  }
+  lagrangian_stage(&s, d, Us, Un, tau); /* S5-S7 */
+  double rho_vac = d->vacuum_frac * d->rho_mean;
+  long long cnt[4] = {0, 0, 0, 0};
+  for (int k = s.g[2]; k < s.g[2] + s.n[2]; k++)
+    for (int j = s.g[1]; j < s.g[1] + s.n[1]; j++)
+      for (int i = s.g[0]; i < s.g[0] + s.n[0]; i++) {
+        size_t g = gidx(&s, i, j, k);
+        double u[NFIELD];
+        for (int f = 0; f < NFIELD; f++) u[f] = Un[f][g];
+        cnt[energy_correction(u, rho_vac)]++; /* S8 */
+        for (int f = 0; f < NFIELD; f++) Un[f][g] = u[f];
+      }
+  for (int f = 0; f < NFIELD; f++) gather_interior(&s, Un[f], u_out[f]);
+  if (diag) {
+    memset(diag, 0, sizeof(*diag));
+    diag_of(d, u_out, cfl, diag); /* S10, S11 */
+    diag->n_vacuum = cnt[1] + cnt[3];
+    diag->n_keep_e = cnt[2];
+    diag->n_zero_m = cnt[3];
+  }
+  for (int f = 0; f < NFIELD; f++) {
+    free(Us[f]);
+    free(Un[f]);
+  }
+  return 0;
+}
+
 /* One full step.  u_in, u_out: six interior-only arrays each (may alias: the output is
  * written only at the end).  u_star (optional, may be NULL): receives U* interior.
  * phi (optional): interior-only potential, ghost-filled with the state's boundaries

@@ -355,9 +355,11 @@ __device__ __forceinline__ int correct_energy<float>(float u[6], double rho_vac)
 }
 
 // Boundary handling by index mapping: interior coordinate read for coordinate c of an
-// axis with n cells (outflow: clamp; periodic: wrap; reflecting: mirror, flip = 1).
-// Coordinates further than n outside the domain (only read for cells that produce no
-// output) are clamped into range.
+// axis with n cells (outflow: clamp; periodic: wrap; reflecting: mirror, flip = 1; halo:
+// the cell itself, stored up to kHaloCells beyond the face by the caller -- a neighbouring
+// slab's cells).  Coordinates further than that outside the domain (only read for cells
+// that produce no output) are clamped into range.
+constexpr int kHaloCells = 3;
 __device__ __forceinline__ int bc_map(int c, int n, int lo, int hi, int& flip) {
   flip = 0;
   if ((unsigned)c < (unsigned)n) return c;
@@ -368,6 +370,8 @@ __device__ __forceinline__ int bc_map(int c, int n, int lo, int hi, int& flip) {
   } else if (bc == 2) {
     flip = 1;
     r = c < 0 ? -1 - c : 2 * n - 1 - c;
+  } else if (bc == 3) {
+    return c < 0 ? max(c, -kHaloCells) : min(c, n - 1 + kHaloCells);
   } else {
     r = c;
   }

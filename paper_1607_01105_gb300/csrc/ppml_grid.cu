@@ -31,12 +31,41 @@ namespace {
 
 constexpr int kFinThreads = 512;
 
-// Reduce nblk partials in a fixed order (independent of scheduling) and update the
-// device scalars.  mode: 0 = diagnostics of a state, 1 = after a step.
+// The device scalars from the maxima, sums (times the cell volume) and counts of a state:
+// advance: the state ends a step of tau (t += tau, clipped to t_end; steps + 1).  Then the
+// next CFL step (Sec. 1.1) clipped to the remaining time, and the flags.
+__device__ void apply_scalars(DevScalars* S, double vmax, double cmax, const double* sums,
+                              double nvac, double nbad, int advance, double tau, double cfl,
+                              double hmin, double t_end) {
+  double tn = S->t;
+  if (advance) {
+    tn = S->t + tau;
+    if (t_end > 0.0 && tn > t_end) tn = t_end;
+    S->t = tn;
+    S->steps += 1;
+    S->n_vac = (long long)nvac;
+  }
+  S->vmax = vmax;
+  S->cmax = cmax;
+  for (int f = 0; f < 6; f++) S->sums[f] = sums[f];
+  S->n_bad = (long long)nbad;
+  double dt = cfl * hmin / (vmax + cmax);
+  if (t_end > 0.0 && dt > t_end - tn) dt = t_end - tn;
+  if (!(dt > 0.0)) {
+    dt = 0.0;
+    S->flags |= PPML_FLAG_DT_ZERO;
+  }
+  S->dt = dt;
+  if (nbad > 0.0) S->flags |= PPML_FLAG_NONPHYSICAL;
+}
+
+// Reduce nblk partials in a fixed order (independent of scheduling).  mode 0: diagnostics
+// of a state into the device scalars; 1: after a step; 2: only write the maxima, sums and
+// counts to red[PPML_REDUCE_LEN] (a slab's share, for an all-reduce across slabs).
 __global__ void __launch_bounds__(kFinThreads)
     finalize_kernel(const Partial* __restrict__ P, int nblk, DevScalars* S, double cfl,
                     double hmin, double vol, double t_end, int mode, const double* dt_dev,
-                    double dt_host) {
+                    double dt_host, double* red) {
   __shared__ double sh[kFinThreads][8];
   __shared__ unsigned long long shc[kFinThreads][2];
   const int t = threadIdx.x;
@@ -68,36 +97,38 @@ __global__ void __launch_bounds__(kFinThreads)
     __syncthreads();
   }
   if (t == 0) {
-    double tn = S->t;
-    if (mode == 1) {
-      tn = S->t + tau;
-      if (t_end > 0.0 && tn > t_end) tn = t_end;
-      S->t = tn;
-      S->steps += 1;
-      S->n_vac = (long long)shc[0][0];
+    double sums[6];
+    for (int f = 0; f < 6; f++) sums[f] = sh[0][f] * vol;
+    if (mode == 2) {
+      red[0] = sh[0][6];
+      red[1] = sh[0][7];
+      for (int f = 0; f < 6; f++) red[2 + f] = sums[f];
+      red[8] = (double)shc[0][0];
+      red[9] = (double)shc[0][1];
+      return;
     }
-    S->vmax = sh[0][6];
-    S->cmax = sh[0][7];
-    for (int f = 0; f < 6; f++) S->sums[f] = sh[0][f] * vol;
-    S->n_bad = (long long)shc[0][1];
-    double dt = cfl * hmin / (sh[0][6] + sh[0][7]);
-    if (t_end > 0.0 && dt > t_end - tn) dt = t_end - tn;
-    if (!(dt > 0.0)) {
-      dt = 0.0;
-      S->flags |= PPML_FLAG_DT_ZERO;
-    }
-    S->dt = dt;
-    if (shc[0][1]) S->flags |= PPML_FLAG_NONPHYSICAL;
+    apply_scalars(S, sh[0][6], sh[0][7], sums, (double)shc[0][0], (double)shc[0][1], mode == 1,
+                  tau, cfl, hmin, t_end);
   }
+}
+
+// The device scalars from an all-reduced red[PPML_REDUCE_LEN] (slab decomposition).
+__global__ void apply_reduced_kernel(const double* __restrict__ red, DevScalars* S, int advance,
+                                     const double* dt_dev, double dt_host, double cfl,
+                                     double hmin, double t_end) {
+  if (threadIdx.x != 0) return;
+  const double tau = advance ? (dt_dev ? *dt_dev : dt_host) : 0.0;
+  apply_scalars(S, red[0], red[1], red + 2, red[8], red[9], advance, tau, cfl, hmin, t_end);
 }
 
 }  // namespace
 
 namespace ppml {
 int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
-                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st) {
+                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st,
+                    double* red) {
   finalize_kernel<<<1, kFinThreads, 0, st>>>(P, nblk, S, cfl, hmin, vol, t_end, mode, dt_dev,
-                                             dt_host);
+                                             dt_host, red);
   return ppml_check_launch("finalize_kernel");
 }
 }  // namespace ppml
@@ -141,8 +172,10 @@ int ppml_validate_desc(const ppml_grid_desc* d) {
     if (!(d->h[a] > 0.0) || !isfinite(d->h[a]))
       return ppml_fail(PPML_E_INVAL, "h[%d] = %g must be positive", a, d->h[a]);
     const int lo = d->bc[2 * a], hi = d->bc[2 * a + 1];
-    if (lo < 0 || lo > 2 || hi < 0 || hi > 2)
+    if (lo < 0 || lo > 3 || hi < 0 || hi > 3)
       return ppml_fail(PPML_E_INVAL, "bc of axis %d is not a ppml_bc", a);
+    if ((lo == PPML_BC_HALO || hi == PPML_BC_HALO) && (a != 2 || n[a] < 3))
+      return ppml_fail(PPML_E_INVAL, "halo faces are z faces of an active z axis (axis %d)", a);
     if ((lo == PPML_BC_PERIODIC) != (hi == PPML_BC_PERIODIC))
       return ppml_fail(PPML_E_INVAL, "periodic bc on axis %d must be set on both faces", a);
     if (n[a] == 1 && (lo == PPML_BC_REFLECT || hi == PPML_BC_REFLECT))
@@ -150,6 +183,8 @@ int ppml_validate_desc(const ppml_grid_desc* d) {
     if (n[a] > 1 && n[a] < 3)
       return ppml_fail(PPML_E_INVAL, "axis %d has %d cells (active axes need >= 3)", a, n[a]);
   }
+  if (d->rho_ref < 0.0 || !isfinite(d->rho_ref))
+    return ppml_fail(PPML_E_INVAL, "rho_ref = %g must be >= 0", d->rho_ref);
   if (!(d->gamma > 1.0) || !isfinite(d->gamma))
     return ppml_fail(PPML_E_INVAL, "gamma = %g must be > 1", d->gamma);
   if (!(d->cfl > 0.0 && d->cfl < 1.0)) return ppml_fail(PPML_E_INVAL, "cfl = %g not in (0,1)", d->cfl);
@@ -178,6 +213,20 @@ int ppml_validate_state(const ppml_state* u, const char* what) {
     for (int q = 0; q < 6; q++)
       if (u->lo[f] == u->f[q]) return ppml_fail(PPML_E_INVAL, "%s low part %d aliases a field", what, f);
   }
+  return PPML_OK;
+}
+
+int ppml_desc_has_halo(const ppml_grid_desc* d) {
+  for (int q = 0; q < 6; q++)
+    if (d->bc[q] == PPML_BC_HALO) return 1;
+  return 0;
+}
+
+// Calls that step through the handle's own U* (which has no halo planes) refuse grids with
+// halo faces: their Lagrangian stage would read U* beyond its first and last planes.
+static int no_halo(const ppml_grid* g, const char* what) {
+  if (ppml_desc_has_halo(&g->d))
+    return ppml_fail(PPML_E_INVAL, "%s: the grid has halo faces (use the slab stage calls)", what);
   return PPML_OK;
 }
 
@@ -225,7 +274,7 @@ int run_diag(ppml_grid* g, const ppml_state* u, cudaStream_t st) {
   int rc = launch_diag<T>(A, g->nblk_diag, st);
   if (rc) return rc;
   return launch_finalize(g->partials, g->nblk_diag, g->dev, g->d.cfl, g->hmin, g->vol,
-                         g->d.t_end, 0, nullptr, 0.0, st);
+                         g->d.t_end, 0, nullptr, 0.0, st, nullptr);
 }
 
 template <typename T>
@@ -293,7 +342,7 @@ int run_step(ppml_grid* g, const ppml_state* uin, ppml_state* uout, const T* phi
   if (rc) return rc;
   if (ev) cudaEventRecord(ev[2], st);
   rc = launch_finalize(g->partials, g->nblk_march, g->dev, g->d.cfl, g->hmin, g->vol,
-                       g->d.t_end, 1, dt_dev, dt_host, st);
+                       g->d.t_end, 1, dt_dev, dt_host, st, nullptr);
   if (ev) cudaEventRecord(ev[3], st);
   return rc;
 }
@@ -372,7 +421,7 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
     ppml_free_grid(g);
     return ppml_fail(PPML_E_CUDA, "init: %s", cudaGetErrorString(cudaGetLastError()));
   }
-  g->rho_mean = hs.sums[0] / (g->vol * (double)g->geom.ncell);
+  g->rho_mean = g->d.rho_ref > 0.0 ? g->d.rho_ref : hs.sums[0] / (g->vol * (double)g->geom.ncell);
   g->rho_vac = g->d.vacuum_frac * g->rho_mean;
   *out = g;
   return PPML_OK;
@@ -410,6 +459,7 @@ extern "C" int ppml_poisson_periodic(ppml_grid* g, const void* rho, void* phi, d
   if (!g || !rho || !phi) return ppml_fail(PPML_E_INVAL, "grid, rho or phi is NULL");
   if (rho == phi) return ppml_fail(PPML_E_INVAL, "rho and phi alias");
   if (!isfinite(G)) return ppml_fail(PPML_E_INVAL, "G is not finite");
+  if (ppml_desc_has_halo(&g->d)) return ppml_fail(PPML_E_INVAL, "Poisson solve on a slab");
   const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
   for (int a = 1; a < 3; a++)
     if (n[a] > 1 && fabs(g->d.h[a] - g->d.h[0]) > 1e-12 * g->d.h[0])
@@ -463,6 +513,7 @@ extern "C" int ppml_poisson_isolated(ppml_grid* g, const void* rho, void* phi, d
   if (rho == phi) return ppml_fail(PPML_E_INVAL, "rho and phi alias");
   if (!isfinite(G)) return ppml_fail(PPML_E_INVAL, "G is not finite");
   if (flags & ~PPML_POISSON_PRINTED_RHS) return ppml_fail(PPML_E_INVAL, "unknown flags 0x%x", flags);
+  if (ppml_desc_has_halo(&g->d)) return ppml_fail(PPML_E_INVAL, "Poisson solve on a slab");
   for (int a = 1; a < 3; a++)
     if (fabs(g->d.h[a] - g->d.h[0]) > 1e-12 * g->d.h[0])
       return ppml_fail(PPML_E_INVAL, "the 27-point solve needs equal cell sizes");
@@ -502,8 +553,9 @@ static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, 
                        double dt, void* stream);
 
 // An input and an output state of one call: the grid's type, low parts in both or neither,
-// and no array of one in the other.
-static int check_state_pair(const ppml_grid_desc* d, const ppml_state* a, const ppml_state* b) {
+// and no array of one in the other (rho_shared: b's rho and its low part may be a's).
+static int check_state_pair(const ppml_grid_desc* d, const ppml_state* a, const ppml_state* b,
+                            bool rho_shared = false) {
   int rc = check_state_type(d, a, "u_in");
   if (rc) return rc;
   rc = check_state_type(d, b, "u_out");
@@ -521,8 +573,10 @@ static int check_state_pair(const ppml_grid_desc* d, const ppml_state* a, const 
     pb[6 + f] = b->lo[f];
   }
   for (int i = 0; i < 11; i++)
-    for (int j = 0; j < 11; j++)
+    for (int j = 0; j < 11; j++) {
+      if (rho_shared && i == j && (i == 0 || i == 6)) continue;
       if (pa[i] && pa[i] == pb[j]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");
+    }
   return PPML_OK;
 }
 
@@ -544,7 +598,9 @@ static int step_common(ppml_grid* g, const ppml_state* u_in, ppml_state* u_out, 
                        double dt, void* stream) {
   ppml_clear_error();
   if (!g) return ppml_fail(PPML_E_INVAL, "grid is NULL");
-  int rc = ppml_validate_state(u_in, "u_in");
+  int rc = no_halo(g, "ppml_step");
+  if (rc) return rc;
+  rc = ppml_validate_state(u_in, "u_in");
   if (rc) return rc;
   rc = ppml_validate_state(u_out, "u_out");
   if (rc) return rc;
@@ -566,14 +622,23 @@ extern "C" int ppml_eulerian_stage(ppml_grid* g, const ppml_state* u_in, ppml_st
   if (rc) return rc;
   rc = ppml_validate_state(u_star, "u_star");
   if (rc) return rc;
-  rc = check_state_pair(&g->d, u_in, u_star);
+  rc = check_state_pair(&g->d, u_in, u_star, true);
   if (rc) return rc;
   if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
   const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
   cudaStream_t st = (cudaStream_t)stream;
+  // rho is not changed by the Eulerian stage: a shared rho array is left as it is
+  void* out[6];
+  void* outlo[5];
+  for (int f = 0; f < 6; f++) out[f] = u_star->f[f];
+  for (int f = 0; f < 5; f++) outlo[f] = u_star->lo[f];
+  if (u_star->f[0] == u_in->f[0]) {
+    out[0] = nullptr;
+    outlo[0] = nullptr;
+  }
   return g->d.dtype == PPML_F64
-             ? run_eulerian<double>(g, u_in, u_star->f, u_star->lo, nullptr, dt, dt_dev, st)
-             : run_eulerian<float>(g, u_in, u_star->f, u_star->lo, nullptr, dt, dt_dev, st);
+             ? run_eulerian<double>(g, u_in, out, outlo, nullptr, dt, dt_dev, st)
+             : run_eulerian<float>(g, u_in, out, outlo, nullptr, dt, dt_dev, st);
 }
 
 extern "C" int ppml_conserved_sums(ppml_grid* g, const ppml_state* u, double out[6],
@@ -676,6 +741,8 @@ extern "C" int ppml_grid_tune(ppml_grid* g, const ppml_state* u, int trial_steps
   rc = check_state_type(&g->d, u, "u");
   if (rc) return rc;
   if (trial_steps < 1) return ppml_fail(PPML_E_INVAL, "trial_steps = %d must be >= 1", trial_steps);
+  rc = no_halo(g, "ppml_grid_tune");
+  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t fbytes = (size_t)g->geom.ncell * g->elt;
   // two scratch states (the trials ping-pong between them from a copy of u's fields) and
@@ -743,4 +810,77 @@ extern "C" int ppml_grid_tune(ppml_grid* g, const ppml_state* u, int trial_steps
   if (rc) return rc;
   if (order_out) *order_out = best;
   return PPML_OK;
+}
+
+// ----------------------------------------------------------------- z-slab decomposition
+
+extern "C" int ppml_local_reduce(ppml_grid* g, const ppml_state* u, double* red, void* stream) {
+  ppml_clear_error();
+  if (!g || !red) return ppml_fail(PPML_E_INVAL, "grid or red is NULL");
+  int rc = ppml_validate_state(u, "u");
+  if (rc) return rc;
+  rc = check_state_type(&g->d, u, "u");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  MarchArgs<double> A64 = make_args<double>(g, 0.0, nullptr);
+  MarchArgs<float> A32 = make_args<float>(g, 0.0, nullptr);
+  for (int f = 0; f < 6; f++) {
+    A64.u[f] = (const double*)u->f[f];
+    A32.u[f] = (const float*)u->f[f];
+  }
+  for (int f = 0; f < 5; f++) A32.ulo[f] = (const float*)u->lo[f];
+  rc = g->d.dtype == PPML_F64 ? launch_diag<double>(A64, g->nblk_diag, st)
+                              : launch_diag<float>(A32, g->nblk_diag, st);
+  if (rc) return rc;
+  return launch_finalize(g->partials, g->nblk_diag, g->dev, g->d.cfl, g->hmin, g->vol,
+                         g->d.t_end, 2, nullptr, 0.0, st, red);
+}
+
+extern "C" int ppml_lagrangian_stage(ppml_grid* g, const ppml_state* u_star, ppml_state* u_out,
+                                     double dt, double* red, void* stream) {
+  ppml_clear_error();
+  if (!g || !red) return ppml_fail(PPML_E_INVAL, "grid or red is NULL");
+  int rc = ppml_validate_state(u_star, "u_star");
+  if (rc) return rc;
+  rc = ppml_validate_state(u_out, "u_out");
+  if (rc) return rc;
+  rc = check_state_pair(&g->d, u_star, u_out);
+  if (rc) return rc;
+  if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
+  const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g->d.dtype == PPML_F64) {
+    MarchArgs<double> L = make_args<double>(g, dt, dt_dev);
+    for (int f = 0; f < 6; f++) {
+      L.u[f] = (const double*)u_star->f[f];
+      L.out[f] = (double*)u_out->f[f];
+    }
+    rc = launch_lagrangian<double>(L, g->nblk_launch, st);
+  } else {
+    MarchArgs<float> L = make_args<float>(g, dt, dt_dev);
+    for (int f = 0; f < 6; f++) {
+      L.u[f] = (const float*)u_star->f[f];
+      L.out[f] = (float*)u_out->f[f];
+    }
+    if (ppml_state_has_lo(u_star))
+      for (int f = 0; f < 5; f++) {
+        L.ulo[f] = (const float*)u_star->lo[f];
+        L.outlo[f] = (float*)u_out->lo[f];
+      }
+    rc = launch_lagrangian<float>(L, g->nblk_launch, st);
+  }
+  if (rc) return rc;
+  return launch_finalize(g->partials, g->nblk_march, g->dev, g->d.cfl, g->hmin, g->vol,
+                         g->d.t_end, 2, dt_dev, dt, st, red);
+}
+
+extern "C" int ppml_apply_reduced(ppml_grid* g, const double* red, int advance, double dt,
+                                  void* stream) {
+  ppml_clear_error();
+  if (!g || !red) return ppml_fail(PPML_E_INVAL, "grid or red is NULL");
+  if (!isfinite(dt)) return ppml_fail(PPML_E_INVAL, "dt is not finite");
+  const double* dt_dev = dt > 0.0 ? nullptr : &g->dev->dt;
+  apply_reduced_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(red, g->dev, advance ? 1 : 0, dt_dev, dt,
+                                                           g->d.cfl, g->hmin, g->d.t_end);
+  return ppml_check_launch("apply_reduced_kernel");
 }

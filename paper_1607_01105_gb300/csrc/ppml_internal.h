@@ -14,6 +14,8 @@ int ppml_check_launch(const char* what);
 // Argument checks shared by the entry points (defined in ppml_grid.cu).
 int ppml_validate_desc(const ppml_grid_desc* d);
 int ppml_validate_state(const ppml_state* u, const char* what);
+// Whether a descriptor has halo faces (a slab of a z-decomposed grid).
+int ppml_desc_has_halo(const ppml_grid_desc* d);
 // Number of non-NULL low-part pointers of a state (0 or 5 once validated).
 int ppml_state_has_lo(const ppml_state* u);
 

@@ -38,7 +38,8 @@ int launch_batch_cluster(T* rho, T* m, T* en, T* ei, BatchLo<T> lo, InstDev* ins
 
 // Deterministic reduction of per-CTA partials into the step scalars (ppml_grid.cu).
 int launch_finalize(const Partial* P, int nblk, DevScalars* S, double cfl, double hmin, double vol,
-                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st);
+                    double t_end, int mode, const double* dt_dev, double dt_host, cudaStream_t st,
+                    double* red);
 
 // explicit specializations live in ppml_kern_f32.cu / ppml_kern_f64.cu
 #define PPML_DECLARE_LAUNCHERS(R)                                                            \

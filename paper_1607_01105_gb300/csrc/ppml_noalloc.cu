@@ -117,7 +117,7 @@ int step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in, ppml_state* u_
   rc = launch_lagrangian<T>(A, nblk, st);
   if (rc) return rc;
   rc = launch_finalize(partials, nblk, S, d->cfl, hmin, d->h[0] * d->h[1] * d->h[2], 0.0, 1,
-                       nullptr, dt, st);
+                       nullptr, dt, st, nullptr);
   if (rc) return rc;
   if (out9) {
     DevScalars hs;
@@ -157,6 +157,8 @@ extern "C" int ppml_step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in
                                    "(no low parts)");
   if (d->t_end > 0.0)
     return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc keeps no simulated time: t_end must be 0");
+  if (ppml_desc_has_halo(d))
+    return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc: halo faces need the slab stage calls");
   for (int f = 0; f < 6; f++)
     for (int q = 0; q < 6; q++)
       if (u_in->f[f] == u_out->f[q]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");

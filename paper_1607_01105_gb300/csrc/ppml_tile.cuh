@@ -98,9 +98,15 @@ __device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, const int tiles
   t.i0 = tc[0] * TB;
   t.j0 = tc[1] * TB;
   t.k0 = tc[2] * TB;
+  // fast: no cell within TH of the tile needs a map (halo faces hold their cells in the
+  // arrays, at the same strides, so they count as inside)
   const int o[3] = {t.i0, t.j0, t.k0};
   bool f = true;
-  for (int a = 0; a < 3; a++) f = f && g.n[a] > 1 && o[a] - TH >= 0 && o[a] + TB + TH <= g.n[a];
+  for (int a = 0; a < 3; a++) {
+    const bool lo_ok = o[a] - TH >= 0 || g.bc[2 * a] == 3;
+    const bool hi_ok = o[a] + TB + TH <= g.n[a] || (g.bc[2 * a + 1] == 3 && o[a] + TB <= g.n[a]);
+    f = f && g.n[a] > 1 && lo_ok && hi_ok;
+  }
   t.fast = f;
   return t;
 }
@@ -786,6 +792,15 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
 
 // ====================================================================== Eulerian stage
 
+// eq. SCHintenEulerian: rho eps - (gamma - 1) rho eps th (V+ - V-), one rounding order for
+// every code path (FP32: one FMA; FP64: as written, the checker's order).
+__device__ __forceinline__ float eps_update(float ei, float gm1, float dv) {
+  return fmaf(-(gm1 * ei), dv, ei);
+}
+__device__ __forceinline__ double eps_update(double ei, double gm1, double dv) {
+  return ei - gm1 * ei * dv;
+}
+
 template <typename T>
 struct EulTileSmem {
   T r[SLAB];   // rho along the sweep axis
@@ -943,7 +958,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         } else {
           A.out[4][idx] = en[q] - S.apv[ai];
         }
-        A.out[5][idx] = ei[q] - gm1 * ei[q] * S.av[ai];
+        A.out[5][idx] = eps_update(ei[q], gm1, S.av[ai]);
       }
     }
     return;
@@ -961,7 +976,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     if (A.phi) {
       GridGeom gp = g;  // Phi: zero-gradient at reflecting walls, like at outflow faces
       for (int q = 0; q < 6; q++)
-        if (gp.bc[q] == 2) gp.bc[q] = 0;
+        if (gp.bc[q] == 2 || gp.bc[q] == 3) gp.bc[q] = 0;
       T m[3] = {A.out[1][idx], A.out[2][idx], A.out[3][idx]};
       const T m0[3] = {A.u[1][idx], A.u[2][idx], A.u[3][idx]};
 #pragma unroll 1
@@ -998,7 +1013,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     } else {
       A.out[4][idx] = en;
     }
-    A.out[5][idx] = ei0 - gm1 * ei0 * dvs;
+    A.out[5][idx] = eps_update(ei0, gm1, dvs);
   }
 }
 

@@ -21,7 +21,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 PPML_OK, PPML_E_INVAL, PPML_E_CUDA, PPML_E_NONPHYSICAL, PPML_E_TIMEOUT, PPML_E_NOMEM = range(6)
 PPML_F32, PPML_F64 = 0, 1
-OUTFLOW, PERIODIC, REFLECT = 0, 1, 2
+OUTFLOW, PERIODIC, REFLECT, HALO = 0, 1, 2, 3
+HALO_PLANES = 3     # planes behind a halo face (z-slab decomposition)
+REDUCE_LEN = 10     # max|v|, max c, six sums, vacuum and non-physical counts
 FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
 FIRST_ORDER, VHAT_1PT = 1, 2  # scheme variants (ppml_grid_desc.flags)
 EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppml_eulerian_stage",
@@ -30,7 +32,8 @@ EXPORTED = ("ppml_init_grid", "ppml_free_grid", "ppml_cfl_dt", "ppml_step", "ppm
             "ppml_profile", "ppml_kernel_times", "ppml_step_noalloc", "ppml_step_phi",
             "ppml_poisson_periodic", "ppml_poisson_isolated", "ppml_batch_tune",
             "ppml_batch_set_threads", "ppml_fourier_amplitudes", "ppml_fma_peak",
-            "ppml_batch_set_split", "ppml_batch_plan", "ppml_grid_tune", "ppml_grid_set_order")
+            "ppml_batch_set_split", "ppml_batch_plan", "ppml_grid_tune", "ppml_grid_set_order",
+            "ppml_local_reduce", "ppml_lagrangian_stage", "ppml_apply_reduced")
 TILE_ORDERS = 4  # launch orders of the stage kernels' tiles (ppml_grid_tune)
 NOALLOC_MAX_CELLS = 262144
 POISSON_PRINTED_RHS = 1  # isolated solve with the right-hand side exactly as printed
@@ -40,7 +43,8 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double * 3), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("bc", ctypes.c_int * 6), ("dtype", ctypes.c_int),
-                ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double), ("flags", ctypes.c_int)]
+                ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double), ("flags", ctypes.c_int),
+                ("rho_ref", ctypes.c_double)]
 
 
 class State(ctypes.Structure):
@@ -91,6 +95,10 @@ _lib.ppml_step_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(Stat
 _lib.ppml_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.ppml_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.ppml_grid_set_order.argtypes = [_vp, ctypes.c_int]
+_lib.ppml_local_reduce.argtypes = [_vp, ctypes.POINTER(State), _vp, _vp]
+_lib.ppml_lagrangian_stage.argtypes = [_vp, ctypes.POINTER(State), ctypes.POINTER(State), ctypes.c_double,
+                                       _vp, _vp]
+_lib.ppml_apply_reduced.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_double, _vp]
 _lib.ppml_grid_tune.argtypes = [_vp, ctypes.POINTER(State), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_double), _vp]
 
@@ -144,7 +152,7 @@ class Grid:
     """Handle over ppml_init_grid / ppml_step / ppml_cfl_dt / ppml_read_diag."""
 
     def __init__(self, n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, u0=None,
-                 vacuum_frac=1e-5, t_end=0.0, stream=None, flags=0):
+                 vacuum_frac=1e-5, t_end=0.0, stream=None, flags=0, rho_ref=0.0):
         d = GridDesc()
         d.nx, d.ny, d.nz = (int(x) for x in n)
         for a in range(3):
@@ -156,13 +164,14 @@ class Grid:
         d.vacuum_frac = float(vacuum_frac)
         d.t_end = float(t_end)
         d.flags = int(flags)
+        d.rho_ref = float(rho_ref)
         self.desc = d
         self.n = tuple(int(x) for x in n)
         self.cells = self.n[0] * self.n[1] * self.n[2]
         self.dtype = int(dtype)
         self.tdtype = torch_dtype(dtype)
         self._h = ctypes.c_void_p()
-        st = _state(u0, self.tdtype, self.cells)
+        st = u0 if isinstance(u0, State) else _state(u0, self.tdtype, self.cells)
         _check(_lib.ppml_init_grid(ctypes.byref(d), ctypes.byref(st), _stream(stream),
                                    ctypes.byref(self._h)))
 
@@ -230,6 +239,23 @@ class Grid:
         _check(_lib.ppml_eulerian_stage(self._h, ctypes.byref(a), ctypes.byref(b), float(dt),
                                         _stream(stream)))
 
+    # z-slab decomposition: the state arguments are State structures (their pointers lead
+    # the interior planes of halo-padded arrays); red is a CUDA float64 tensor of REDUCE_LEN
+    def local_reduce(self, st, red, stream=None):
+        _check(_lib.ppml_local_reduce(self._h, ctypes.byref(st), red.data_ptr(), _stream(stream)))
+
+    def lagrangian_stage(self, st_star, st_out, dt, red, stream=None):
+        _check(_lib.ppml_lagrangian_stage(self._h, ctypes.byref(st_star), ctypes.byref(st_out),
+                                          float(dt), red.data_ptr(), _stream(stream)))
+
+    def eulerian_stage_ptrs(self, st_in, st_star, dt, stream=None):
+        _check(_lib.ppml_eulerian_stage(self._h, ctypes.byref(st_in), ctypes.byref(st_star),
+                                        float(dt), _stream(stream)))
+
+    def apply_reduced(self, red, advance, dt=0.0, stream=None):
+        _check(_lib.ppml_apply_reduced(self._h, red.data_ptr(), 1 if advance else 0, float(dt),
+                                       _stream(stream)))
+
     def conserved_sums(self, u, stream=None):
         st = _state(u, self.tdtype, self.cells)
         out = (ctypes.c_double * 6)()
@@ -274,7 +300,7 @@ class Grid:
 
 
 def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1e-5, t_end=0.0,
-              flags=0):
+              flags=0, rho_ref=0.0):
     d = GridDesc()
     d.nx, d.ny, d.nz = (int(x) for x in n)
     for a in range(3):
@@ -286,6 +312,7 @@ def make_desc(n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, vacuum_frac=1
     d.vacuum_frac = float(vacuum_frac)
     d.t_end = float(t_end)
     d.flags = int(flags)
+    d.rho_ref = float(rho_ref)
     return d
 
 
