@@ -392,6 +392,24 @@ def reference_arm(args):
     return 0
 
 
+def profile_run(args):
+    """K plain FP32 steps of the n^3 point blast, untimed (for ncu captures: launch k of a
+    stage kernel is step k's)."""
+    import torch
+    from paper_1607_01105_gb300 import inputs, ppml
+    torch.cuda.set_device(0)
+    pb = inputs.point_blast_3d(args.n)
+    u = ppml.to_device(pb.u, ppml.PPML_F32)
+    v = [torch.empty_like(x) for x in u]
+    grid = ppml.Grid(pb.n, pb.h, pb.gamma, pb.cfl, pb.bc, ppml.PPML_F32, u0=u)
+    for _ in range(args.steps):
+        grid.step(u, v, 0.0)
+        u, v = v, u
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": args.n, "steps": args.steps, "t": grid.diag()["t"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +422,9 @@ def main():
     ap.add_argument("--cpu-table", action="store_true")
     ap.add_argument("--cpu-table-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--disk-n", type=int, default=512, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only run --steps plain FP32 steps of the --n^3 point blast (x-major "
+                         "tiles, device CFL step) and exit: the program a profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -412,6 +433,8 @@ def main():
         return 0
     if args.cpu_table:
         return cpu_table(args)
+    if args.profile_run:
+        return profile_run(args)
 
     import torch
     import torch.distributed as dist
