@@ -50,7 +50,7 @@ OPS_LAG = 18 * 62 + 57 + 30 + 12 + 42
 OPS_EUL = 3 * (84 + 15 + 32 + 9 + 8 + 1) + 6
 # DRAM bytes of one Lagrangian launch measured by ncu (dram__bytes_read + write, one launch
 # of the 256^3 point blast, the timed workload itself; see profiles/).
-NCU_LAG_DRAM_BYTES_256 = 494.68e6 + 386.93e6
+NCU_LAG_DRAM_BYTES_256 = 493.80e6 + 386.67e6
 SMS, FP32_LANES = 152, 128
 
 
@@ -410,6 +410,74 @@ def profile_run(args):
     return 0
 
 
+def slab_bench(args):
+    """The FP32 step of the n^3 point blast split into z slabs (one per rank; on one GPU,
+    --emulate-ranks slabs driven by this process): exchange of U^n and U* halo planes,
+    both stages, all-reduce of the CFL maxima and sums, per step.  Strong scaling: value =
+    the whole grid's cell-updates / max-over-ranks time."""
+    import torch
+    import torch.distributed as dist
+    from paper_1607_01105_gb300 import inputs, ppml, slab
+    import oracle  # mean density of the input only (the vacuum threshold's reference)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local if world > 1 else 0)
+    if world > 1:
+        dist.init_process_group("nccl")
+    pb = inputs.point_blast_3d(args.n)
+    rho_ref = oracle.mean_density(pb.u)
+    if world > 1:
+        layouts = [slab.SlabLayout(pb.n, pb.bc, world, rank)]
+        comm = slab.DistComm(dist, layouts[0])
+    else:
+        k = max(1, args.emulate_ranks)
+        layouts = [slab.SlabLayout(pb.n, pb.bc, k, r) for r in range(k)]
+        comm = slab.LocalComm(layouts)
+    stages = [slab.Stages(ppml, L, pb.h, pb.gamma, pb.cfl, ppml.PPML_F32,
+                          [slab.pad_field(L, u, torch.float32, "cuda") for u in pb.u], rho_ref)
+              for L in layouts]
+    slab.start(stages, comm)
+    for _ in range(args.warmup):
+        slab.step(stages, comm)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as cs:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            slab.step(stages, comm)
+        e1.record(stream)
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, torch.device("cuda", torch.cuda.current_device()))
+    if rank == 0:
+        value = pb.cells * args.steps / (ms * 1e-3) / 1e6
+        nslab = world if world > 1 else len(layouts)
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"point_blast_3d {args.n}^3 split into {nslab} z slabs "
+                                   f"({[L.nz for L in layouts] if world == 1 else 'one per rank'} "
+                                   f"planes), FP32; halo exchange of U^n and U*, all-reduce of the "
+                                   f"CFL maxima and sums every step",
+                       "global_batch": 1, "seq_len": 0,
+                       "parallelism": f"z-slabs x{world}" if world > 1 else
+                                      f"{nslab} slabs in one process (plane copies)"},
+            "gpu_launches": 4 * len(layouts) * args.steps,  # two stages, reduce, apply
+            "clocks": cs.summary()}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,6 +490,10 @@ def main():
     ap.add_argument("--cpu-table", action="store_true")
     ap.add_argument("--cpu-table-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--disk-n", type=int, default=512, help=argparse.SUPPRESS)
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="ranks run replicas of the grid (default) or z slabs of one grid")
+    ap.add_argument("--emulate-ranks", type=int, default=2,
+                    help="--decomp slab on one GPU: slabs driven by this one process")
     ap.add_argument("--profile-run", action="store_true",
                     help="only run --steps plain FP32 steps of the --n^3 point blast (x-major "
                          "tiles, device CFL step) and exit: the program a profiler captures")
@@ -435,6 +507,8 @@ def main():
         return cpu_table(args)
     if args.profile_run:
         return profile_run(args)
+    if args.decomp == "slab":
+        return slab_bench(args)
 
     import torch
     import torch.distributed as dist

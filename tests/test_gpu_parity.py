@@ -910,6 +910,28 @@ def test_disk_fourier_amplitudes_match_oracle(n, dtype):
             grid.fourier_amplitudes(u[0], *bad)
 
 
+@pytest.mark.slow
+def test_config5_disk_64_fp64_one_orbit():
+    """Config 5 setup at 64^3 in FP64 over one orbital period at half the disk radius (about
+    750 steps with self-gravity from the periodic Poisson solve plus the halo potential; the
+    oracle's step sizes): within 1e-10 of the oracle, the pre-registered check of config 5
+    at reduced size (the disk is gravitationally unstable, Q = 0.8, so round-off grows)."""
+    from oracle import poisson
+    pb = inputs.galactic_disk(n=64)
+    g = oracle_grid(pb)
+    t_orb = pb.extra["t_orb"]
+    ref, dts, t = pb.u, [], 0.0
+    while t < t_orb:
+        phi = poisson.solve_periodic(ref[0], pb.h[0]) + pb.extra["phi_halo"]
+        dt = min(oracle.cfl_dt(g, ref), t_orb - t)
+        dts.append(dt)
+        ref, dg = oracle.step(g, ref, dt, phi=phi)
+        t += dt
+    assert len(dts) > 500
+    got, grid = _disk_run_gpu(pb, F64, dts)
+    compare(got, ref, TOL64)
+
+
 def test_config5_disk_64_fp64_isolated_gravity():
     """The disk with self-gravity from the isolated-boundary solve (the paper's isolated
     galaxy setup) at 64^3 in FP64, 12 steps against the oracle (1e-10)."""
