@@ -12,6 +12,8 @@
 // the domain faces take the unmapped fast path.  The unsplit sums over axes are taken in
 // the order x, y, z.
 #pragma once
+#include <type_traits>
+
 #include "../../include/ppml.h"
 #include "ppml_common.cuh"
 
@@ -32,6 +34,11 @@ __device__ __forceinline__ int box_at(int i, int j, int k) {
   return (i + TH) + BRP * (j + TH) + BPP * (k + TH);
 }
 __device__ __forceinline__ int acc_at(int i, int j, int k) { return i + ARP * j + APP * k; }
+
+template <int V>
+using IntC = std::integral_constant<int, V>;
+template <bool V>
+using BoolC = std::integral_constant<bool, V>;
 
 struct TileGeom {
   int i0, j0, k0;
@@ -346,6 +353,33 @@ __device__ __forceinline__ void stage_box_fast(T* box, const T* __restrict__ src
   }
 }
 
+// Face velocities as the sweeps read them.  FP64: v^ itself (the flux and the Courant
+// number are formed as the checker forms them).  FP32: w = v^ th / 2 (th = tau / h), so
+// that |w| is half the Courant number y and w times the upwind state is half of th times
+// the flux (both exact rescalings of v^ th): the per-field products by th disappear, the
+// sweeps accumulate half divergences and the update subtracts twice their sum.
+__device__ __forceinline__ float vh_stored(float v, float th) { return v * (0.5f * th); }
+__device__ __forceinline__ double vh_stored(double v, double) { return v; }
+// The flux divergence summed over axes from what the sweeps accumulated (exact).
+__device__ __forceinline__ float divergence_sum(float half_sum) { return 2.0f * half_sum; }
+__device__ __forceinline__ double divergence_sum(double sum) { return sum; }
+
+// FP32 flux through a face of eq. fluxonlagrangestage from w = v^ th / 2: w times the
+// upwind state, the left cell's mean over its right fraction y when w >= 0, else the right
+// cell's mean over its left fraction y, written as base + c1 D + c2 S with
+// c1 = -+ y/2, c2 = (y/2)(1 - 2y/3) (the characteristic averages expanded).
+__device__ __forceinline__ float half_flux_f32(float w, float R_l, float D_l, float S_l,
+                                              float L_r, float D_r, float S_r) {
+  const bool from_left = w >= 0.0f;
+  const float hy = fabsf(w);
+  const float c2 = hy * fmaf(-4.0f / 3.0f, hy, 1.0f);
+  const float c1 = from_left ? -hy : hy;
+  const float base = from_left ? R_l : L_r;
+  const float D = from_left ? D_l : D_r;
+  const float S = from_left ? S_l : S_r;
+  return w * fmaf(c1, D, fmaf(c2, S, base));
+}
+
 // One line of the Lagrangian stage for any axis.  Field values: core[p cs] for p in
 // [0, 16), halo[h SLP] for the positions -3..-1 (h = 0..2) and 16..18 (h = 3..5).  Face
 // velocities vh[c TN], c = 0..16 (face between cells c-1 and c).  MODE 0: acc = div;
@@ -354,13 +388,15 @@ __device__ __forceinline__ void stage_box_fast(T* box, const T* __restrict__ src
 // parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
 // peeled and the steady state is a loop unrolled by two.  DF (MODE 2): when dstlo is
 // non-NULL the field is a double-float value whose low part srclo[c gs] is read and the
-// update is added in double-float (dst the high part, dstlo the low part).
-template <typename T, int MODE, bool FLAT, bool DF = false>
-__device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, const T* vh, T th,
+// update is added in double-float (dst the high part, dstlo the low part).  CS: the core
+// stride of the sweep axis as a compile-time constant (immediate shared-memory offsets).
+template <typename T, int MODE, bool FLAT, bool DF, int CS>
+__device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* vh, T th,
                                          double tau, double h, T* acc, bool have_acc,
                                          T* __restrict__ dst, long long gs, int nvalid,
                                          const T* __restrict__ srclo = nullptr,
                                          T* __restrict__ dstlo = nullptr) {
+  constexpr int cs = CS;
   T qa = halo[0], qb = halo[SLP];  // q(p-2), q(p-1)
   T qn = halo[2 * SLP];            // p = -1
   T da = limited_slope(qa, qb, qn);
@@ -385,9 +421,14 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
   dn = limited_slope(qa, qb, qn);
   fn = face_value(qa, qb, da, dn);
   P = FLAT ? flat_parabola(qa) : parabola(qa, fa, fn);  // cell 0
-  T v = vh[0];
-  T y = Prec<T>::courant(tabs(v), tau, h, th);
-  T Fp = v * upwind_state(v >= T(0), PR, PD, PS, P.L, P.D, P.S, y);
+  T Fp;
+  if constexpr (sizeof(T) == 4) {
+    Fp = half_flux_f32(vh[0], PR, PD, PS, P.L, P.D, P.S);
+  } else {
+    const T v = vh[0];
+    const T y = Prec<T>::courant(tabs(v), tau, h, th);
+    Fp = v * upwind_state(v >= T(0), PR, PD, PS, P.L, P.D, P.S, y);
+  }
   PR = P.R;
   PD = P.D;
   PS = P.S;
@@ -400,17 +441,23 @@ __device__ __forceinline__ void lag_line(const T* core, int cs, const T* halo, c
     const T dnn = limited_slope(qa, qb, qnew);
     const T fnn = face_value(qa, qb, da, dnn);
     const Parab<T> Pn = FLAT ? flat_parabola(qa) : parabola(qa, fa, fnn);  // cell c+1
-    const T vv = vh[(c + 1) * TN];              // face between cells c and c+1
-    const T yy = Prec<T>::courant(tabs(vv), tau, h, th);
-    const T F = vv * upwind_state(vv >= T(0), PR, PD, PS, Pn.L, Pn.D, Pn.S, yy);
-    const T d = th * (F - Fp);
+    const T vv = vh[(c + 1) * TN];  // face between cells c and c+1
+    T F, d;
+    if constexpr (sizeof(T) == 4) {
+      F = half_flux_f32(vv, PR, PD, PS, Pn.L, Pn.D, Pn.S);
+      d = F - Fp;  // half of th (F+ - F-)
+    } else {
+      const T yy = Prec<T>::courant(tabs(vv), tau, h, th);
+      F = vv * upwind_state(vv >= T(0), PR, PD, PS, Pn.L, Pn.D, Pn.S, yy);
+      d = th * (F - Fp);
+    }
     const int o = c * cs;
     if (MODE == 0) {
       acc[o] = d;
     } else if (MODE == 1) {
       acc[o] = acc[o] + d;
     } else if (c < nvalid) {
-      const T upd = have_acc ? acc[o] + d : d;
+      const T upd = divergence_sum(have_acc ? acc[o] + d : d);
       if constexpr (DF) {
         if (dstlo) {
           float hi, lo;
@@ -552,12 +599,12 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
     T vh0[TB + 1];
     line_face_velocities(vbox(0), rbox, 0, a, b, one_point, vh0);
 #pragma unroll
-    for (int q = 0; q <= TB; q++) S.vh[0][q][tid] = vh0[q];
+    for (int q = 0; q <= TB; q++) S.vh[0][q][tid] = vh_stored(vh0[q], th[0]);
   }
 #pragma unroll
   for (int q = 0; q <= TB; q++) {
-    if (act[1]) S.vh[1][q][tid] = vh1[q];
-    if (act[2]) S.vh[2][q][tid] = vh2[q];
+    if (act[1]) S.vh[1][q][tid] = vh_stored(vh1[q], th[1]);
+    if (act[2]) S.vh[2][q][tid] = vh_stored(vh2[q], th[2]);
   }
   __syncthreads();
 
@@ -652,30 +699,39 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
       const int cb = acc_at(li, lj, lk);
-      const int cs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
       const T* halo = &S.fld[halo_at(ax, 0, tid)];
       const T* vhl = &S.vh[ax][0][tid];
       const T* srclo = DF && f < 5 ? A.ulo[f] + zline0 : nullptr;
       T* dstlo = DF && f < 5 ? A.outlo[f] + zline0 : nullptr;
-      if (first_order) {
-        if (ax == 2)
-          lag_line<T, 2, true, DF>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
-                                   mode == 1, A.out[f] + zline0, g.nxy, nvalid_z, srclo, dstlo);
-        else if (mode == 0)
-          lag_line<T, 0, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
-                               false, nullptr, 0, 0);
+      const T* core = &S.fld[cb];
+      T* acc = &S.acc[cb];
+      // one instantiation per (axis, mode): x is always the first sweep (mode 0), y the
+      // first or the second, z the last (MODE 2: finish into the output)
+      auto sweep = [&](auto mode_c, auto flat_c, auto cs_c) {
+        constexpr int M = decltype(mode_c)::value;
+        constexpr bool FL = decltype(flat_c)::value;
+        constexpr int C = decltype(cs_c)::value;
+        if constexpr (M == 2)
+          lag_line<T, 2, FL, DF, C>(core, halo, vhl, th[2], tau, A.h[2], acc, mode == 1,
+                                    A.out[f] + zline0, g.nxy, nvalid_z, srclo, dstlo);
         else
-          lag_line<T, 1, true>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
-                               false, nullptr, 0, 0);
-      } else if (ax == 2)
-        lag_line<T, 2, false, DF>(&S.fld[cb], cs, halo, vhl, th[2], tau, A.h[2], &S.acc[cb],
-                                  mode == 1, A.out[f] + zline0, g.nxy, nvalid_z, srclo, dstlo);
-      else if (mode == 0)
-        lag_line<T, 0, false>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
-                              false, nullptr, 0, 0);
+          lag_line<T, M, FL, false, C>(core, halo, vhl, th[ax], tau, A.h[ax], acc, false,
+                                       nullptr, 0, 0);
+      };
+      auto sweep_ax = [&](auto flat_c) {
+        if (ax == 2)
+          sweep(IntC<2>(), flat_c, IntC<APP>());
+        else if (ax == 1 && mode == 1)
+          sweep(IntC<1>(), flat_c, IntC<ARP>());
+        else if (ax == 1)
+          sweep(IntC<0>(), flat_c, IntC<ARP>());
+        else
+          sweep(IntC<0>(), flat_c, IntC<1>());
+      };
+      if (first_order)
+        sweep_ax(BoolC<true>());
       else
-        lag_line<T, 1, false>(&S.fld[cb], cs, halo, vhl, th[ax], tau, A.h[ax], &S.acc[cb],
-                              false, nullptr, 0, 0);
+        sweep_ax(BoolC<false>());
       mode = 1;
       if (ax < 2) __syncthreads();
     }
@@ -683,7 +739,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       for (int c = 0; c < nvalid_z; c++) {
         const int o = acc_at(a, b, c);
         const long long idx = zline0 + g.nxy * c;
-        const T upd = mode == 1 ? S.acc[o] : T(0);
+        const T upd = mode == 1 ? divergence_sum(S.acc[o]) : T(0);
         if constexpr (DF) {
           if (f < 5) {
             float hi, lo;
