@@ -51,7 +51,10 @@ template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
 // Appendix, Step 1: limited slope delta_m q_i.  Branch-free: min(|dq|, 2 min(|r|, |l|))
-// equals min(|dq|, 2|r|, 2|l|) exactly (doubling is exact), and r l > 0 implies dq != 0.
+// equals min(|dq|, 2|r|, 2|l|) exactly (doubling is exact), and r l > 0 implies q is
+// strictly monotone, so dq != 0 (up to underflow to a zero of either sign) and the sign
+// copy equals the test dq > 0; where r l <= 0 the result is +0 whatever the signs of the
+// zeros inside, so fabs (an operand modifier) gives the values of the sign test.
 template <typename T>
 __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
   const T dq = T(0.5) * (qp - qm);
@@ -59,9 +62,8 @@ __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
   if (sizeof(T) == 8) {  // FP64: evaluate only what is used (same values)
     if (!(r * l > T(0))) return T(0);
   }
-  const T m = fmin(tabs(dq), T(2) * fmin(tabs(r), tabs(l)));
-  const T sm = dq > T(0) ? m : -m;
-  return r * l > T(0) ? sm : T(0);
+  const T m = fmin(fabs(dq), T(2) * fmin(fabs(r), fabs(l)));
+  return r * l > T(0) ? copysign(m, dq) : T(0);
 }
 
 // Appendix, Step 1: 4th-order face value q_{i+1/2} from the cell values and limited slopes.
@@ -87,8 +89,9 @@ __device__ __forceinline__ Parab<T> parabola(T q0, T L, T R) {
   }
   const T D = R - L;
   const T S = T(6) * (q0 - T(0.5) * (L + R));
+  // at most one fix: D S > D D >= 0 >= -(D D) excludes D S < -(D D)
   const bool fixL = D * S > D * D;
-  const bool fixR = !fixL && D * S < -(D * D);
+  const bool fixR = D * S < -(D * D);
   const T Ln = flat ? q0 : (fixL ? T(3) * q0 - T(2) * R : L);
   const T Rn = flat ? q0 : (fixR ? T(3) * q0 - T(2) * L : R);
   Parab<T> p;

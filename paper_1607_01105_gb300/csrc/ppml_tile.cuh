@@ -437,12 +437,11 @@ __device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* 
   da = dn;
   fa = fn;
   // steady state: p = 3..18 emits cell c = p-3
-  auto step = [&](T qnew, int c) {
+  auto step = [&](T qnew, T vv, int c) {
     const T dnn = limited_slope(qa, qb, qnew);
     const T fnn = face_value(qa, qb, da, dnn);
     const Parab<T> Pn = FLAT ? flat_parabola(qa) : parabola(qa, fa, fnn);  // cell c+1
-    const T vv = vh[(c + 1) * TN];  // face between cells c and c+1
-    T F, d;
+    T F, d;  // through the face between cells c and c+1
     if constexpr (sizeof(T) == 4) {
       F = half_flux_f32(vv, PR, PD, PS, Pn.L, Pn.D, Pn.S);
       d = F - Fp;  // half of th (F+ - F-)
@@ -480,10 +479,23 @@ __device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* 
     da = dnn;
     fa = fnn;
   };
+  // inputs one step ahead: position c + 3 and face c + 1 of step c are loaded in step c - 1
+  T q_in = core[3 * cs], v_in = vh[TN];
 #pragma unroll 2
-  for (int c = 0; c < TB - 3; c++) step(core[(c + 3) * cs], c);
+  for (int c = 0; c < TB - 4; c++) {
+    const T q = q_in, v = v_in;
+    q_in = core[(c + 4) * cs];
+    v_in = vh[(c + 2) * TN];
+    step(q, v, c);
+  }
 #pragma unroll 1
-  for (int c = TB - 3; c < TB; c++) step(halo[(c - TB + 6) * SLP], c);
+  for (int c = TB - 4; c < TB - 1; c++) {
+    const T q = q_in, v = v_in;
+    q_in = halo[(c - TB + 7) * SLP];  // positions 16..18
+    v_in = vh[(c + 2) * TN];          // faces 14..16
+    step(q, v, c);
+  }
+  step(q_in, v_in, TB - 1);
 }
 
 // Face velocities v^ of line (a, b) along axis ax (faces 0..16, face c between cells c-1
