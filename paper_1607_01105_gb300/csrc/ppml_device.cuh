@@ -11,7 +11,8 @@
 // Precision policy.  The double instantiation is compiled without FMA contraction and
 // evaluates every expression in the same order as the FP64 checker (x/6, 2y/3,
 // (speed * tau) / h), so the FP64 path reproduces it bit for bit.  The float
-// instantiation uses the cheaper forms (x * (1/6), y * (2/3), speed * (tau/h)) and FMAs.
+// instantiation uses the cheaper forms (doubled slopes, x * (1/12), y * (2/3),
+// speed * (tau/h)) and FMAs.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,7 +24,6 @@ struct Prec;
 
 template <>
 struct Prec<float> {
-  static __device__ __forceinline__ float div6(float x) { return x * (1.0f / 6.0f); }
   static __device__ __forceinline__ float two_thirds(float y) { return y * (2.0f / 3.0f); }
   // Courant number of a signal speed s: s * tau / h with th = tau / h precomputed.
   static __device__ __forceinline__ float courant(float s, double /*tau*/, double /*h*/,
@@ -34,7 +34,6 @@ struct Prec<float> {
 
 template <>
 struct Prec<double> {
-  static __device__ __forceinline__ double div6(double x) { return x / 6.0; }
   static __device__ __forceinline__ double two_thirds(double y) { return 2.0 * y / 3.0; }
   static __device__ __forceinline__ double courant(double s, double tau, double h,
                                                    double /*th*/) {
@@ -55,21 +54,32 @@ __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 // strictly monotone, so dq != 0 (up to underflow to a zero of either sign) and the sign
 // copy equals the test dq > 0; where r l <= 0 the result is +0 whatever the signs of the
 // zeros inside, so fabs (an operand modifier) gives the values of the sign test.
+// The FP32 instantiation returns twice the slope, min(|q+ - q-|, 4|r|, 4|l|) with its sign
+// (every scaling exact), which face_value expects: the halving is folded into its 1/6.
 template <typename T>
 __device__ __forceinline__ T limited_slope(T qm, T q0, T qp) {
-  const T dq = T(0.5) * (qp - qm);
   const T r = qp - q0, l = q0 - qm;
-  if (sizeof(T) == 8) {  // FP64: evaluate only what is used (same values)
+  if constexpr (sizeof(T) == 8) {  // FP64: evaluate only what is used (same values)
+    const T dq = T(0.5) * (qp - qm);
     if (!(r * l > T(0))) return T(0);
+    const T m = fmin(fabs(dq), T(2) * fmin(fabs(r), fabs(l)));
+    return copysign(m, dq);
+  } else {
+    const T dq2 = qp - qm;
+    const T m2 = fmin(fabs(dq2), T(4) * fmin(fabs(r), fabs(l)));
+    return r * l > T(0) ? copysign(m2, dq2) : T(0);
   }
-  const T m = fmin(fabs(dq), T(2) * fmin(fabs(r), fabs(l)));
-  return r * l > T(0) ? copysign(m, dq) : T(0);
 }
 
-// Appendix, Step 1: 4th-order face value q_{i+1/2} from the cell values and limited slopes.
+// Appendix, Step 1: 4th-order face value q_{i+1/2} from the cell values and limited slopes
+// (FP32: from the doubled slopes of limited_slope, (d1 - d0) / 12 = the (d1 - d0) / 6 of
+// the halved values).
 template <typename T>
 __device__ __forceinline__ T face_value(T q0, T q1, T d0, T d1) {
-  return T(0.5) * (q0 + q1) - Prec<T>::div6(d1 - d0);
+  if constexpr (sizeof(T) == 8)
+    return T(0.5) * (q0 + q1) - (d1 - d0) / 6.0;
+  else
+    return T(0.5) * (q0 + q1) - (d1 - d0) * (1.0f / 12.0f);
 }
 
 // Appendix, Steps 2-3: parabola of a cell from its value and its two face values.

@@ -955,21 +955,31 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     }
     if (async_ok) cp_async_wait_all();
     __syncthreads();
+    // the thread's line along ax: accumulator base and stride, global offset and stride,
+    // and the number of its cells inside the domain, formed once per axis
+    int li, lj, lk;
+    line_cell(ax, 0, a, b, li, lj, lk);
+    const int acc0 = acc_at(li, lj, lk);
+    const int acs = ax == 0 ? 1 : (ax == 1 ? ARP : APP);
+    const long long gst = ax == 0 ? 1 : (ax == 1 ? (long long)g.n[0] : g.nxy);
+    const long long gbase =
+        (long long)(tg.i0 + li) + (long long)g.n[0] * (tg.j0 + lj) + g.nxy * (tg.k0 + lk);
+    const int lo_ax = ax == 0 ? tg.i0 : (ax == 1 ? tg.j0 : tg.k0);
+    const int nvalid = in_domain(g, tg, li, lj, lk) ? min(TB, g.n[ax] - lo_ax) : 0;
+    T* const om = A.out[1 + ax] + gbase;
     auto emit = [&](int c, T dm, T dpv, T dv) {
-      int i, j, k;
-      line_cell(ax, c, a, b, i, j, k);
-      const int ai = acc_at(i, j, k);
+      const int ai = acc0 + c * acs;
       S.apv[ai] = first ? dpv : S.apv[ai] + dpv;
       S.av[ai] = first ? dv : S.av[ai] + dv;
-      if (in_domain(g, tg, i, j, k)) {
-        const long long idx = (long long)(tg.i0 + i) + (long long)g.n[0] * (tg.j0 + j) + g.nxy * (tg.k0 + k);
+      if (c < nvalid) {
+        const long long off = gst * c;
         if constexpr (DF) {
           float hi, lo;
-          df_sub(S.m[slab_at(c, a, b)], A.ulo[1 + ax][idx], dm, hi, lo);
-          A.out[1 + ax][idx] = hi;
-          A.outlo[1 + ax][idx] = lo;
+          df_sub(S.m[slab_at(c, a, b)], A.ulo[1 + ax][gbase + off], dm, hi, lo);
+          om[off] = hi;
+          A.outlo[1 + ax][gbase + off] = lo;
         } else {
-          A.out[1 + ax][idx] = S.m[slab_at(c, a, b)] - dm;
+          om[off] = S.m[slab_at(c, a, b)] - dm;
         }
       }
     };
