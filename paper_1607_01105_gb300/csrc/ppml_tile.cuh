@@ -181,10 +181,12 @@ __device__ __forceinline__ Parab<T> flat_parabola(T q) {
 
 // Eulerian sweep along one line: v(p), pr(p), r(p) give v_a, p and rho at position p.
 // emit(c, dm, dpv, dv) is called for cells c = 0..15 with dm = th (P+ - P-),
-// dpv = th (P+V+ - P-V-), dv = th (V+ - V-).
-template <typename T, bool FLAT, typename VF, typename PF, typename RF, typename EF>
+// dpv = th (P+V+ - P-V-), dv = th (V+ - V-).  hook(p) is called before step p = -1..18
+// reads position p, and with p = 19 after the last step; positions below p - 3 are no
+// longer read at that point (step p reads positions p, p - 2 and p - 3).
+template <typename T, bool FLAT, typename VF, typename PF, typename RF, typename EF, typename HF>
 __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th, double tau,
-                                               double h, EF emit) {
+                                               double h, EF emit, HF hook) {
   T va = v(-3), vb = v(-2), pa = pr(-3), pb = pr(-2);
   T dva = T(0), fva = T(0), dpa = T(0), fpa = T(0);
   T vR = T(0), vD = T(0), vS = T(0), pR = T(0), pD = T(0), pS = T(0);
@@ -193,6 +195,7 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
   T sprev = T(0);                // FP32: sqrt(rho) of cell p-3
 #pragma unroll
   for (int p = -1; p <= TB + 2; p++) {
+    hook(p);
     const T vn = v(p), pn = pr(p);
     const T dvn = limited_slope(va, vb, vn), dpn = limited_slope(pa, pb, pn);
     T fvn = T(0), fpn = T(0);
@@ -249,6 +252,7 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
     dpa = dpn;
     fpa = fpn;
   }
+  hook(TB + 3);
 }
 
 // ===================================================================== Lagrangian stage
@@ -904,13 +908,20 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const long long zline0e =
       (long long)(tg.i0 + a) + (long long)g.n[0] * (tg.j0 + b) + g.nxy * tg.k0;
   bool first = true;
+  // With asynchronous copies a sweep fetches the next active axis's slab entries of its own
+  // line into the slots it no longer reads (every line's entries are read by its owner
+  // alone): positions -3..5, 6..11 and 12..18 in three commit groups, awaited before the
+  // next sweep, before its step 6 and before its step 12.
+  bool staged = false;  // this axis's entries were fetched during the previous sweep
 #pragma unroll 1
   for (int ax = 0; ax < 3; ax++) {
     if (!act[ax]) continue;
     // stage rho, m_ax, rho eps along the axis: position p in [-3, 18], transverse
     // (s % 16, s / 16); on interior tiles the y and z lines are copied by their owners
     // (lanes consecutive in x), the x slab walks x fastest
-    if (async_ok && tg.fast && ax > 0) {
+    if (staged) {
+      cp_async_wait_group<2>();
+    } else if (async_ok && tg.fast && ax > 0) {
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
       const long long lb =
@@ -953,8 +964,54 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
         S.p[o] = A.u[5][c];
       }
     }
-    if (async_ok) cp_async_wait_all();
+    if (async_ok && !staged) cp_async_wait_all();
     __syncthreads();
+    // the next active axis, fetched during this sweep
+    int nax = -1;
+    for (int q = 2; q > ax; q--)
+      if (act[q]) nax = q;
+    const bool pf = async_ok && nax >= 0;
+    long long nbase = 0, nst = 0;
+    if (pf) {
+      int ni, nj, nk;
+      line_cell(nax, 0, a, b, ni, nj, nk);
+      if (tg.fast) {
+        nbase = (long long)(tg.i0 + ni) + (long long)g.n[0] * (tg.j0 + nj) + g.nxy * (tg.k0 + nk);
+        nst = nax == 1 ? (long long)g.n[0] : g.nxy;
+      } else {  // the two transverse map entries of the line
+        nbase = (nax == 0 ? 0 : maps.off[0][ni + TH]) + (nax == 1 ? 0 : maps.off[1][nj + TH]) +
+                (nax == 2 ? 0 : maps.off[2][nk + TH]);
+      }
+    }
+    auto fetch = [&](int q) {  // position q of the thread's line along nax
+      const long long go = tg.fast ? nbase + nst * q : nbase + maps.off[nax][q + TH];
+      const int o = slab_at(q, a, b);
+      cp_async_elem(&S.r[o], A.u[0] + go);
+      cp_async_elem(&S.m[o], A.u[1 + nax] + go);
+      cp_async_elem(&S.p[o], A.u[5] + go);
+    };
+    const bool was_staged = staged;
+    auto hook = [&](int p) {
+      if (was_staged) {
+        if (p == 6) cp_async_wait_group<1>();
+        if (p == 12) {
+          if (pf)
+            cp_async_wait_group<1>();
+          else
+            cp_async_wait_group<0>();
+        }
+      }
+      if (pf) {
+        if (p >= 1 && p <= TB + 2) fetch(p - 4);
+        if (p == 9 || p == 15) cp_async_commit();
+        if (p == TB + 3) {
+#pragma unroll
+          for (int q = TB - 1; q < TB + TH; q++) fetch(q);
+          cp_async_commit();
+        }
+      }
+    };
+    staged = pf;
     // the thread's line along ax: accumulator base and stride, global offset and stride,
     // and the number of its cells inside the domain, formed once per axis
     int li, lj, lk;
@@ -993,9 +1050,9 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     auto pq = [&](int p) { return gm1 * S.p[slab_at(p, a, b)]; };
     auto rq = [&](int p) { return S.r[slab_at(p, a, b)]; };
     if (A.flags & PPML_FIRST_ORDER)
-      sweep_eulerian<T, true>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit);
+      sweep_eulerian<T, true>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit, hook);
     else
-      sweep_eulerian<T, false>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit);
+      sweep_eulerian<T, false>(vq, pq, rq, gamma, th[ax], tau, A.h[ax], emit, hook);
     first = false;
     __syncthreads();
   }
