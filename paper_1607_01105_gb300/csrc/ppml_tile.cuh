@@ -697,21 +697,19 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       }
     }
     // three commit groups when asynchronous: core + x halo, y halo, z halo; each sweep
-    // waits only for the group it reads, so the later copies overlap the earlier sweeps
+    // waits only for the group it reads, so the later copies overlap the earlier sweeps.
+    // Every thread stages its own core column and halo rows, and the halo rows are read
+    // by their owner alone: the halo waits need no barrier, and the barrier below (which
+    // publishes the core) also orders this field's acc writes after the previous field's
+    // z sweep, so no barrier ends a field.
     if (async_ok) cp_async_wait_group<2>();
     __syncthreads();
     int mode = 0;
 #pragma unroll 1
     for (int ax = 0; ax < 3; ax++) {
       if (!act[ax]) continue;
-      if (async_ok && ax == 1) {  // y halo (the barrier after the x sweep orders it)
-        cp_async_wait_group<1>();
-        __syncthreads();
-      }
-      if (async_ok && ax == 2) {
-        cp_async_wait_group<0>();
-        __syncthreads();
-      }
+      if (async_ok && ax == 1) cp_async_wait_group<1>();  // the thread's own y halo
+      if (async_ok && ax == 2) cp_async_wait_group<0>();  // and z halo
       int li, lj, lk;
       line_cell(ax, 0, a, b, li, lj, lk);
       const int cb = acc_at(li, lj, lk);
@@ -768,7 +766,6 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
         A.out[f][idx] = S.fld[o] - upd;
       }
     }
-    __syncthreads();
   }
 
   // ---- energy correction (Sec. 1.4), CFL maxima and sums of the thread's z line
