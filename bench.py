@@ -50,7 +50,7 @@ OPS_LAG = 18 * 62 + 57 + 30 + 12 + 42
 OPS_EUL = 3 * (84 + 15 + 32 + 9 + 8 + 1) + 6
 # DRAM bytes of one Lagrangian launch measured by ncu (dram__bytes_read + write, one launch
 # of the 256^3 point blast, the timed workload itself; see profiles/).
-NCU_LAG_DRAM_BYTES_256 = 493.80e6 + 386.67e6
+NCU_LAG_DRAM_BYTES_256 = 486.10e6 + 381.00e6
 SMS, FP32_LANES = 152, 128
 
 
@@ -749,7 +749,7 @@ def main():
                          "algorithmic_ops_per_cell": OPS_LAG,
                          "traffic": NCU_LAG_DRAM_BYTES_256 if args.n == 256 else None,
                          "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                         "launch of the 256^3 point blast (52.5 B/cell; 48 "
+                                         "launch of the 256^3 point blast (51.7 B/cell; 48 "
                                          "algorithmic)",
                          "kernel_ms": {"eulerian": keul, "lagrangian": klag, "finalize": kfin},
                          "eulerian": {"achieved": eul_ops, "frac": eul_ops / alu_peak,

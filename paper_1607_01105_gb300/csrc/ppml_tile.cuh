@@ -436,6 +436,7 @@ __device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* 
   PR = P.R;
   PD = P.D;
   PS = P.S;
+  T qc = qa;  // q(c) for c = 0: cell c's value, the base of its update (MODE 2)
   qa = qb;
   qb = qn;
   da = dn;
@@ -464,16 +465,17 @@ __device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* 
       if constexpr (DF) {
         if (dstlo) {
           float hi, lo;
-          df_sub(core[o], srclo[gs * c], upd, hi, lo);
+          df_sub(qc, srclo[gs * c], upd, hi, lo);
           dst[gs * c] = hi;
           dstlo[gs * c] = lo;
         } else {
-          dst[gs * c] = core[o] - upd;
+          dst[gs * c] = qc - upd;
         }
       } else {
-        dst[gs * c] = core[o] - upd;
+        dst[gs * c] = qc - upd;
       }
     }
+    qc = qa;
     Fp = F;
     PR = Pn.R;
     PD = Pn.D;
@@ -485,7 +487,7 @@ __device__ __forceinline__ void lag_line(const T* core, const T* halo, const T* 
   };
   // inputs one step ahead: position c + 3 and face c + 1 of step c are loaded in step c - 1
   T q_in = core[3 * cs], v_in = vh[TN];
-#pragma unroll 2
+#pragma unroll 4
   for (int c = 0; c < TB - 4; c++) {
     const T q = q_in, v = v_in;
     q_in = core[(c + 4) * cs];
