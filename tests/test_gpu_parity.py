@@ -86,6 +86,12 @@ CASES = {
     "rough_2d": lambda: inputs.random_rough(n=(37, 29, 1), bc=(0, 0, 1, 1, 0, 0)),
     "rough_1d": lambda: inputs.random_rough(n=(301, 1, 1), bc=(0, 0, 0, 0, 0, 0)),
     "min_cells_3d": lambda: inputs.random_rough(n=(3, 3, 3), bc=(1,) * 6),
+    # x inactive (the Eulerian sweeps y then z) and y inactive (x then z, the next-axis
+    # fetch skipping y); a grid with an interior tile (1, 1, 1), whose copies take the
+    # unmapped paths
+    "rough_yz_plane": lambda: inputs.random_rough(n=(1, 23, 19), bc=(0, 0, 1, 1, 0, 0)),
+    "rough_xz_plane": lambda: inputs.random_rough(n=(21, 1, 18), bc=(1, 1, 0, 0, 2, 2)),
+    "rough_interior_3d": lambda: inputs.random_rough(n=(37, 35, 36)),
     "point_blast_16": lambda: inputs.point_blast_3d(n=16),
 }
 
@@ -154,7 +160,8 @@ def test_scheme_variants_fp64_bitwise(case, flags):
     assert [int(np.count_nonzero(got[f] != ref[f])) for f in range(6)] == [0] * 6
 
 
-@pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_2d", "point_blast_16"])
+@pytest.mark.parametrize("case", ["smooth_mixed_3d", "rough_2d", "point_blast_16",
+                                  "rough_interior_3d", "rough_yz_plane"])
 def test_step_fp32_single_step(case):
     """One FP32 step from the same (FP32-representable) input as the oracle."""
     pb = CASES[case]()
