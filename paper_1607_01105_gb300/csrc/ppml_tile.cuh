@@ -193,23 +193,26 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
   T Vp = T(0), Pp = T(0);
   T rprev = T(0), pprev = T(0);  // rho, p of cell p-3
   T sprev = T(0);                // FP32: sqrt(rho) of cell p-3
-#pragma unroll
-  for (int p = -1; p <= TB + 2; p++) {
+  // step p; WARM: one of the first four steps (p constant), which skip the parts whose
+  // inputs have not arrived; the steady steps p = 3..18 run as a rolled loop (a smaller
+  // body for the instruction cache)
+  auto step = [&](int p, auto warm_c) {
+    constexpr bool W = decltype(warm_c)::value;
     hook(p);
     const T vn = v(p), pn = pr(p);
     const T dvn = limited_slope(va, vb, vn), dpn = limited_slope(pa, pb, pn);
     T fvn = T(0), fpn = T(0);
-    if (p >= 0) {
+    if (!W || p >= 0) {
       fvn = face_value(va, vb, dva, dvn);
       fpn = face_value(pa, pb, dpa, dpn);
     }
-    if (p >= 1) {
+    if (!W || p >= 1) {
       const Parab<T> Pv = FLAT ? flat_parabola(va) : parabola(va, fva, fvn);  // cell p-2
       const Parab<T> Pq = FLAT ? flat_parabola(pa) : parabola(pa, fpa, fpn);
       const T rc = r(p - 2);
       if constexpr (sizeof(T) == 4) {
         const float sc = sqrt_approx(rc);
-        if (p >= 2) {  // face between cells p-3 and p-2
+        if (!W || p >= 2) {  // face between cells p-3 and p-2
           float lam, Z, hrz;
           face_constants_f32(rprev, rc, sprev, sc, pprev, pa, gamma, lam, Z, hrz);
           const float y = lam * th;
@@ -217,12 +220,12 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
           const float pls = avg_right(pR, pD, pS, y), prs = avg_left(Pq.L, Pq.D, Pq.S, y);
           const float V = 0.5f * (vls + vrs) + (pls - prs) * hrz;
           const float P = 0.5f * (pls + prs) + 0.5f * Z * (vls - vrs);
-          if (p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
+          if (!W || p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
           Vp = V;
           Pp = P;
         }
         sprev = sc;
-      } else if (p >= 2) {
+      } else if (!W || p >= 2) {
         // face between cells p-3 and p-2
         T lam, Z;
         face_constants(rprev, rc, pprev, pa, gamma, lam, Z);
@@ -230,7 +233,7 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
         T V, P;
         riemann_vp(avg_right(vR, vD, vS, y), avg_left(Pv.L, Pv.D, Pv.S, y),
                    avg_right(pR, pD, pS, y), avg_left(Pq.L, Pq.D, Pq.S, y), Z, V, P);
-        if (p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
+        if (!W || p >= 3) emit(p - 3, th * (P - Pp), th * (P * V - Pp * Vp), th * (V - Vp));
         Vp = V;
         Pp = P;
       }
@@ -251,7 +254,11 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
     pb = pn;
     dpa = dpn;
     fpa = fpn;
-  }
+  };
+#pragma unroll
+  for (int p = -1; p < 3; p++) step(p, BoolC<true>());
+#pragma unroll 2
+  for (int p = 3; p <= TB + 2; p++) step(p, BoolC<false>());
   hook(TB + 3);
 }
 
