@@ -194,8 +194,8 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
   T rprev = T(0), pprev = T(0);  // rho, p of cell p-3
   T sprev = T(0);                // FP32: sqrt(rho) of cell p-3
   // step p; WARM: one of the first four steps (p constant), which skip the parts whose
-  // inputs have not arrived; the steady steps p = 3..18 run as a rolled loop (a smaller
-  // body for the instruction cache)
+  // inputs have not arrived; in FP32 the steady steps p = 3..18 run as a loop unrolled by
+  // two (a smaller body for the instruction cache)
   auto step = [&](int p, auto warm_c) {
     constexpr bool W = decltype(warm_c)::value;
     hook(p);
@@ -257,8 +257,13 @@ __device__ __forceinline__ void sweep_eulerian(VF v, PF pr, RF r, T gamma, T th,
   };
 #pragma unroll
   for (int p = -1; p < 3; p++) step(p, BoolC<true>());
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll 2
-  for (int p = 3; p <= TB + 2; p++) step(p, BoolC<false>());
+    for (int p = 3; p <= TB + 2; p++) step(p, BoolC<false>());
+  } else {  // FP64 is bound by its FP64 pipe, not by instruction fetch: fully unrolled
+#pragma unroll
+    for (int p = 3; p <= TB + 2; p++) step(p, BoolC<false>());
+  }
   hook(TB + 3);
 }
 
