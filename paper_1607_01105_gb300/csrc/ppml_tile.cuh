@@ -2,7 +2,8 @@
 //
 // A CTA of 256 threads owns a 16^3 tile.  Thread t = a + 16 b owns one line per axis
 // (x line (j, k) = (a, b); y line (i, k) = (a, b); z line (i, j) = (a, b)).  Each line is
-// swept by a fully unrolled register pipeline: when position p arrives, the limited slope
+// swept by a register pipeline (warm-up steps peeled, the steady steps a partly unrolled
+// loop, its inputs loaded a step ahead): when position p arrives, the limited slope
 // at p-1, the face value at p-3/2, the parabola of p-2 and the flux through the face
 // p-5/2 are formed (Appendix Steps 1-3, characteristic averages), so every quantity along
 // the line is computed once; the 3-cell halo costs 6 extra positions per 16 cells.
@@ -402,7 +403,7 @@ __device__ __forceinline__ float half_flux_f32(float w, float R_l, float D_l, fl
 // 1: acc += div; 2: dst[c gs] = core - (acc + div) for c < nvalid (acc only if have_acc).
 // The pipeline forms, when position p arrives, the slope at p-1, the face at p-3/2, the
 // parabola of cell p-2 and the flux through face p-5/2; the warm-up positions -1..2 are
-// peeled and the steady state is a loop unrolled by two.  DF (MODE 2): when dstlo is
+// peeled and the steady state is a loop unrolled by four.  DF (MODE 2): when dstlo is
 // non-NULL the field is a double-float value whose low part srclo[c gs] is read and the
 // update is added in double-float (dst the high part, dstlo the low part).  CS: the core
 // stride of the sweep axis as a compile-time constant (immediate shared-memory offsets).
