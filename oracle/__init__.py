@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ppml_oracle.c")
 _LIB = os.path.join(_HERE, "libppml_oracle.so")
 
-BC_OUTFLOW, BC_PERIODIC, BC_REFLECT = 0, 1, 2
+BC_OUTFLOW, BC_PERIODIC, BC_REFLECT, BC_INFLOW = 0, 1, 2, 4
 FIRST_ORDER, VHAT_1PT = 1, 2  # scheme variants (Sec. 1.1 first order; 1-point face velocity)
 FIELDS = ("rho", "mx", "my", "mz", "en", "ei")
 
@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 class _Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 6), ("h", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("vacuum_frac", ctypes.c_double),
-                ("rho_mean", ctypes.c_double), ("flags", ctypes.c_int)]
+                ("rho_mean", ctypes.c_double), ("flags", ctypes.c_int),
+                ("inflow", (ctypes.c_double * 6) * 6)]
 
 
 class Diag(ctypes.Structure):
@@ -90,7 +91,9 @@ def lib():
 
 @dataclass
 class Grid:
-    """Problem statement: interior cells, spacing, gamma, boundaries (order -x,+x,-y,+y,-z,+z)."""
+    """Problem statement: interior cells, spacing, gamma, boundaries (order -x,+x,-y,+y,-z,+z).
+    inflow: {face: six conserved values} for the faces whose bc is BC_INFLOW (their ghost
+    cells hold that state)."""
     n: tuple  # (nx, ny, nz)
     h: tuple  # (hx, hy, hz)
     gamma: float
@@ -99,6 +102,7 @@ class Grid:
     vacuum_frac: float = 1e-5
     rho_mean: float = 1.0
     flags: int = 0
+    inflow: dict = field(default_factory=dict)
 
     def desc(self) -> _Desc:
         d = _Desc()
@@ -111,6 +115,12 @@ class Grid:
         d.vacuum_frac = float(self.vacuum_frac)
         d.rho_mean = float(self.rho_mean)
         d.flags = int(self.flags)
+        for q in range(6):
+            if self.bc[q] == BC_INFLOW:
+                if q not in self.inflow:
+                    raise ValueError(f"face {q} is an inflow face without a prescribed state")
+                for f in range(6):
+                    d.inflow[q][f] = float(self.inflow[q][f])
         return d
 
 

@@ -6,7 +6,7 @@
  *
  * It follows the paper's algorithm step by step, cell by cell, on ghost-padded
  * arrays, in the order the paper states it:
- *   S0  ghost fill of U^n (outflow / periodic / reflecting, axes in order x, y, z)
+ *   S0  ghost fill of U^n (outflow / periodic / reflecting / inflow, axes in order x, y, z)
  *   S1  PPML parabolas of v_a and p                 (Appendix, Steps 1-3, eq. A1)
  *   S2  face Riemann solve with modified Roe averages and parabola averages
  *                                                   (Sec. "Low-dissipation hydrodynamic
@@ -56,7 +56,7 @@
 #define NG 3           /* ghost layers per side */
 #define NFIELD 6       /* rho, m_x, m_y, m_z, rho E, rho eps */
 enum { F_RHO = 0, F_MX = 1, F_MY = 2, F_MZ = 3, F_EN = 4, F_EI = 5 };
-enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
+enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2, BC_INFLOW = 4 };
 
 typedef struct {
   int n[3];            /* interior cells per axis (x fastest in memory) */
@@ -68,6 +68,8 @@ typedef struct {
   int flags;           /* ORACLE_FIRST_ORDER: piecewise-constant states (Sec. 1.1);
                           ORACLE_VHAT_1PT: face velocity from the line only (no 9-point
                           template, the 1-point variant the paper compares against) */
+  double inflow[6][NFIELD]; /* per face: the prescribed state of its ghost cells (rho,
+                               m_x, m_y, m_z, rho E, rho eps), read where bc is BC_INFLOW */
 } oracle_desc;
 #define ORACLE_FIRST_ORDER 1
 #define ORACLE_VHAT_1PT 2
@@ -147,7 +149,10 @@ static int bc_source(int c, int n, int bc_lo, int bc_hi, int* flip) {
 }
 
 /* S0 / S4: fill the NG ghost layers of one field, axes in order x, y, z; each axis pass
- * runs over the full padded extent of the other axes so edges and corners are filled. */
+ * runs over the full padded extent of the other axes so edges and corners are filled.
+ * An inflow face's ghost layers take its prescribed state (field >= 0; a potential,
+ * field -1, is filled with the boundaries of its own descriptor).  At an edge or a corner
+ * a later axis's pass overwrites an earlier one's ghosts. */
 static void fill_ghosts(const gshape* s, const oracle_desc* d, double* q, int field) {
   for (int a = 0; a < 3; a++) {
     int b = (a + 1) % 3, c = (a + 2) % 3;
@@ -160,11 +165,16 @@ static void fill_ghosts(const gshape* s, const oracle_desc* d, double* q, int fi
         for (int g = 0; g < s->g[a]; g++) {
           int ghosts[2] = {g - s->g[a], s->n[a] + g}; /* interior coords of a low and a high ghost */
           for (int side = 0; side < 2; side++) {
+            const size_t dst = base + st * (size_t)(ghosts[side] + s->g[a]);
+            if (d->bc[2 * a + side] == BC_INFLOW && field >= 0) {
+              q[dst] = d->inflow[2 * a + side][field];
+              continue;
+            }
             int flip;
             int src = bc_source(ghosts[side], s->n[a], d->bc[2 * a], d->bc[2 * a + 1], &flip);
             double v = q[base + st * (size_t)(src + s->g[a])];
             if (flip && field == F_MX + a) v = -v;
-            q[base + st * (size_t)(ghosts[side] + s->g[a])] = v;
+            q[dst] = v;
           }
         }
       }
@@ -715,7 +725,7 @@ int oracle_step(const oracle_desc* d, double* const u_in[NFIELD], double* const 
   if (phi_in) {
     oracle_desc dphi = *d;
     for (int q = 0; q < 6; q++)
-      if (dphi.bc[q] == BC_REFLECT) dphi.bc[q] = BC_OUTFLOW;
+      if (dphi.bc[q] == BC_REFLECT || dphi.bc[q] == BC_INFLOW) dphi.bc[q] = BC_OUTFLOW;
     phi = (double*)calloc(s.cells, sizeof(double));
     scatter_interior(&s, phi_in, phi);
     fill_ghosts(&s, &dphi, phi, -1);
