@@ -58,7 +58,10 @@ typedef enum {
   PPML_BC_OUTFLOW = 0,
   PPML_BC_PERIODIC = 1,
   PPML_BC_REFLECT = 2,
-  PPML_BC_HALO = 3 /* z faces only: a slab of a z-decomposed grid (see "z-slab decomposition") */
+  PPML_BC_HALO = 3, /* z faces only: a slab of a z-decomposed grid (see "z-slab decomposition") */
+  PPML_BC_INFLOW = 4 /* the face's ghost cells hold a prescribed state (ppml_grid_desc.inflow);
+                        at an edge or corner of two ghost regions the later axis (x, y, z order)
+                        decides; not on a grid with a reflecting face */
 } ppml_bc;
 
 /* scheme variants (ppml_grid_desc.flags) */
@@ -87,6 +90,9 @@ typedef struct {
   int flags;          /* PPML_FIRST_ORDER | PPML_VHAT_1PT variants; 0 = the PPML scheme */
   double rho_ref;     /* > 0: reference density of the vacuum threshold (a slab passes the
                          whole grid's mean); 0: the mean of the initial state */
+  double inflow[6][6]; /* per face, for PPML_BC_INFLOW faces: the conserved state of its ghost
+                          cells (rho > 0, m_x, m_y, m_z, rho E, rho eps > 0; finite); other
+                          faces' entries are not read */
 } ppml_grid_desc;
 
 /* Six device pointers: rho, m_x, m_y, m_z, rho E, rho eps (see conventions), and for FP32
@@ -293,7 +299,8 @@ int ppml_kernel_times(ppml_grid* g, double ms[3], long long* steps);
  *             returns PPML_E_INVAL; d->t_end must be 0 (the call keeps no simulated time,
  *             so there is nothing to clip the step against)
  *   u_in      input state, not modified; u_out output state (no aliasing); plain float
- *             or double states only (low parts are PPML_E_INVAL here)
+ *             or double states only (low parts are PPML_E_INVAL here); grids with
+ *             PPML_BC_INFLOW faces are PPML_E_INVAL (their states live in a grid handle)
  *   dt        step size, > 0 (there is no device-resident step here)
  *   rho_mean  mean initial density, > 0 (reference of the vacuum threshold)
  *   out       NULL, or nine doubles receiving the CFL step of u_out, max|v|, max c and the

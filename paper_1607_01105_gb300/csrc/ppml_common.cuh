@@ -42,6 +42,8 @@ struct MarchArgs {
   int tile_order;         // launch order of the tiles (TileOrder)
   int any_reflect;       // a reflecting wall exists (its sign flips need register copies)
   int flags;             // PPML_FIRST_ORDER, PPML_VHAT_1PT
+  const T* inflow;       // [face][field]: the prescribed ghost states of inflow faces
+  int any_inflow;        // an inflow face exists (selects the kernels that read them)
 };
 
 __device__ __forceinline__ double read_tau(const double* dt_dev, double dt_host) {

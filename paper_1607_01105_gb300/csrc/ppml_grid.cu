@@ -140,6 +140,7 @@ struct ppml_grid {
   void* ustar[6];  // [0] unused (rho is not changed by the Eulerian stage)
   void* ustar_lo[5];  // FP32: low parts of U*'s m and rho E ([0] unused)
   Partial* partials;
+  void* inflow;  // 36 values of the state's type: the inflow faces' ghost states [face][field]
   int nblk_march, nblk_diag, npartials;  // tiles (partials of a step), diagnostics blocks
   int tiles_x, tiles_y, tiles_z;
   int tile_order;   // launch order of the stage kernels' tiles (ppml_grid_tune)
@@ -172,8 +173,15 @@ int ppml_validate_desc(const ppml_grid_desc* d) {
     if (!(d->h[a] > 0.0) || !isfinite(d->h[a]))
       return ppml_fail(PPML_E_INVAL, "h[%d] = %g must be positive", a, d->h[a]);
     const int lo = d->bc[2 * a], hi = d->bc[2 * a + 1];
-    if (lo < 0 || lo > 3 || hi < 0 || hi > 3)
+    if (lo < 0 || lo > 4 || hi < 0 || hi > 4)
       return ppml_fail(PPML_E_INVAL, "bc of axis %d is not a ppml_bc", a);
+    for (int side = 0; side < 2; side++) {
+      if (d->bc[2 * a + side] != PPML_BC_INFLOW) continue;
+      const double* s = d->inflow[2 * a + side];
+      bool ok = s[0] > 0.0 && s[5] > 0.0;
+      for (int f = 0; f < 6; f++) ok = ok && isfinite(s[f]);
+      if (!ok) return ppml_fail(PPML_E_INVAL, "inflow state of face %d needs rho > 0, rho eps > 0, finite values", 2 * a + side);
+    }
     if ((lo == PPML_BC_HALO || hi == PPML_BC_HALO) && (a != 2 || n[a] < 3))
       return ppml_fail(PPML_E_INVAL, "halo faces are z faces of an active z axis (axis %d)", a);
     if ((lo == PPML_BC_PERIODIC) != (hi == PPML_BC_PERIODIC))
@@ -183,6 +191,13 @@ int ppml_validate_desc(const ppml_grid_desc* d) {
     if (n[a] > 1 && n[a] < 3)
       return ppml_fail(PPML_E_INVAL, "axis %d has %d cells (active axes need >= 3)", a, n[a]);
   }
+  bool has_inflow = false, has_reflect = false;
+  for (int q = 0; q < 6; q++) {
+    has_inflow = has_inflow || d->bc[q] == PPML_BC_INFLOW;
+    has_reflect = has_reflect || d->bc[q] == PPML_BC_REFLECT;
+  }
+  if (has_inflow && has_reflect)
+    return ppml_fail(PPML_E_INVAL, "inflow faces cannot be combined with reflecting faces");
   if (d->rho_ref < 0.0 || !isfinite(d->rho_ref))
     return ppml_fail(PPML_E_INVAL, "rho_ref = %g must be >= 0", d->rho_ref);
   if (!(d->gamma > 1.0) || !isfinite(d->gamma))
@@ -263,6 +278,9 @@ MarchArgs<T> make_args(const ppml_grid* g, double dt_host, const double* dt_dev)
   A.any_reflect = 0;
   for (int q = 0; q < 6; q++) A.any_reflect |= g->d.bc[q] == PPML_BC_REFLECT;
   A.flags = g->d.flags;
+  A.inflow = (const T*)g->inflow;
+  A.any_inflow = 0;
+  for (int q = 0; q < 6; q++) A.any_inflow |= g->d.bc[q] == PPML_BC_INFLOW;
   return A;
 }
 
@@ -404,11 +422,26 @@ extern "C" int ppml_init_grid(const ppml_grid_desc* d, const ppml_state* u0, voi
     }
   }
   if (cudaMalloc(&g->partials, sizeof(Partial) * (size_t)g->npartials) != cudaSuccess ||
-      cudaMalloc(&g->dev, sizeof(DevScalars)) != cudaSuccess) {
+      cudaMalloc(&g->dev, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMalloc(&g->inflow, 36 * g->elt) != cudaSuccess) {
     ppml_free_grid(g);
     return ppml_fail(PPML_E_NOMEM, "cudaMalloc of reduction scratch failed");
   }
   cudaStream_t st = (cudaStream_t)stream;
+  {  // the inflow states in the state's precision (zeros for faces that are not inflow)
+    double hd[36];
+    float hf[36];
+    for (int q = 0; q < 6; q++)
+      for (int f = 0; f < 6; f++) {
+        hd[6 * q + f] = d->bc[q] == PPML_BC_INFLOW ? d->inflow[q][f] : 0.0;
+        hf[6 * q + f] = (float)hd[6 * q + f];
+      }
+    if (cudaMemcpy(g->inflow, d->dtype == PPML_F64 ? (const void*)hd : (const void*)hf,
+                   36 * g->elt, cudaMemcpyHostToDevice) != cudaSuccess) {
+      ppml_free_grid(g);
+      return ppml_fail(PPML_E_CUDA, "init: inflow states: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+  }
   cudaMemsetAsync(g->dev, 0, sizeof(DevScalars), st);
   rc = d->dtype == PPML_F64 ? run_diag<double>(g, u0, st) : run_diag<float>(g, u0, st);
   if (rc) {
@@ -436,6 +469,7 @@ extern "C" int ppml_free_grid(ppml_grid* g) {
   for (int f = 0; f < 5; f++)
     if (g->ustar_lo[f]) cudaFree(g->ustar_lo[f]);
   if (g->partials) cudaFree(g->partials);
+  if (g->inflow) cudaFree(g->inflow);
   if (g->dev) cudaFree(g->dev);
   if (g->ev) {
     for (int q = 0; q < 4 * ppml_grid::kEvSlots; q++) cudaEventDestroy(g->ev[q]);

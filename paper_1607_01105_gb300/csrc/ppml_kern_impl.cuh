@@ -23,16 +23,22 @@ struct MinBlocks<double> {
 // Double-float states (low parts of rho, m, rho E) exist only in the FP32 path.
 constexpr bool kHasDF = sizeof(PPML_REAL) == 4;
 
-template <bool DF>
-cudaError_t set_stage_smem() {
+template <bool DF, bool INF>
+cudaError_t set_stage_smem_one() {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  cudaError_t e = cudaFuncSetAttribute(lagrangian_tile<PPML_REAL, MB, DF>,
+  cudaError_t e = cudaFuncSetAttribute(lagrangian_tile<PPML_REAL, MB, DF, INF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(LagTileSmem<PPML_REAL>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(eulerian_tile<PPML_REAL, MB, DF>,
+    e = cudaFuncSetAttribute(eulerian_tile<PPML_REAL, MB, DF, INF>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(EulTileSmem<PPML_REAL>));
+  return e;
+}
+template <bool DF>
+cudaError_t set_stage_smem() {
+  cudaError_t e = set_stage_smem_one<DF, false>();
+  if (e == cudaSuccess) e = set_stage_smem_one<DF, true>();
   return e;
 }
 
@@ -47,20 +53,36 @@ int prepare_kernels<PPML_REAL>() {
 template <>
 int launch_eulerian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  if (kHasDF && A.outlo[1])
-    eulerian_tile<PPML_REAL, MB, kHasDF><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
-  else
-    eulerian_tile<PPML_REAL, MB, false><<<nblk, TN, sizeof(EulTileSmem<PPML_REAL>), st>>>(A);
+  constexpr size_t SM = sizeof(EulTileSmem<PPML_REAL>);
+  const bool df = kHasDF && A.outlo[1];
+  if (A.any_inflow) {
+    if (df)
+      eulerian_tile<PPML_REAL, MB, kHasDF, true><<<nblk, TN, SM, st>>>(A);
+    else
+      eulerian_tile<PPML_REAL, MB, false, true><<<nblk, TN, SM, st>>>(A);
+  } else if (df) {
+    eulerian_tile<PPML_REAL, MB, kHasDF, false><<<nblk, TN, SM, st>>>(A);
+  } else {
+    eulerian_tile<PPML_REAL, MB, false, false><<<nblk, TN, SM, st>>>(A);
+  }
   return ppml_check_launch("eulerian_tile");
 }
 
 template <>
 int launch_lagrangian<PPML_REAL>(const MarchArgs<PPML_REAL>& A, int nblk, cudaStream_t st) {
   constexpr int MB = MinBlocks<PPML_REAL>::value;
-  if (kHasDF && A.outlo[0])
-    lagrangian_tile<PPML_REAL, MB, kHasDF><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
-  else
-    lagrangian_tile<PPML_REAL, MB, false><<<nblk, TN, sizeof(LagTileSmem<PPML_REAL>), st>>>(A);
+  constexpr size_t SM = sizeof(LagTileSmem<PPML_REAL>);
+  const bool df = kHasDF && A.outlo[0];
+  if (A.any_inflow) {
+    if (df)
+      lagrangian_tile<PPML_REAL, MB, kHasDF, true><<<nblk, TN, SM, st>>>(A);
+    else
+      lagrangian_tile<PPML_REAL, MB, false, true><<<nblk, TN, SM, st>>>(A);
+  } else if (df) {
+    lagrangian_tile<PPML_REAL, MB, kHasDF, false><<<nblk, TN, SM, st>>>(A);
+  } else {
+    lagrangian_tile<PPML_REAL, MB, false, false><<<nblk, TN, SM, st>>>(A);
+  }
   return ppml_check_launch("lagrangian_tile");
 }
 

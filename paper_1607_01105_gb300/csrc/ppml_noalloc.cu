@@ -159,6 +159,9 @@ extern "C" int ppml_step_noalloc(const ppml_grid_desc* d, const ppml_state* u_in
     return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc keeps no simulated time: t_end must be 0");
   if (ppml_desc_has_halo(d))
     return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc: halo faces need the slab stage calls");
+  for (int q = 0; q < 6; q++)
+    if (d->bc[q] == PPML_BC_INFLOW)
+      return ppml_fail(PPML_E_INVAL, "ppml_step_noalloc: inflow faces need a grid handle");
   for (int f = 0; f < 6; f++)
     for (int q = 0; q < 6; q++)
       if (u_in->f[f] == u_out->f[q]) return ppml_fail(PPML_E_INVAL, "u_in and u_out alias");

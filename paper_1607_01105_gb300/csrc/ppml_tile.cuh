@@ -126,6 +126,7 @@ __device__ __forceinline__ TileGeom tile_geom(const GridGeom& g, const int tiles
 struct TileMaps {
   long long off[3][TW];
   int flip[3][TW];
+  int inflow[3][TW];  // the inflow face whose ghost region the coordinate lies in, or -1
 };
 
 __device__ __forceinline__ void build_maps(TileMaps& M, const GridGeom& g, const TileGeom& t) {
@@ -137,7 +138,43 @@ __device__ __forceinline__ void build_maps(TileMaps& M, const GridGeom& g, const
     const long long stride = ax == 0 ? 1LL : (ax == 1 ? (long long)g.n[0] : g.nxy);
     M.off[ax][c + TH] = (long long)m * stride;
     M.flip[ax][c + TH] = fl << ax;
+    // inflow ghosts only along active axes (an inactive axis has no ghost cells: its
+    // coordinates are clamped onto the one cell)
+    const int gc = o + c;
+    const bool act = g.n[ax] > 1;
+    M.inflow[ax][c + TH] = act && gc < 0 && g.bc[2 * ax] == PPML_BC_INFLOW
+                               ? 2 * ax
+                               : (act && gc >= g.n[ax] && g.bc[2 * ax + 1] == PPML_BC_INFLOW
+                                      ? 2 * ax + 1
+                                      : -1);
   }
+}
+
+// Whether the tile reads a ghost cell of an inflow face (uniform over the CTA).
+__device__ __forceinline__ bool tile_inflow(const GridGeom& g, const TileGeom& t) {
+  const int o[3] = {t.i0, t.j0, t.k0};
+  bool r = false;
+  for (int a = 0; a < 3; a++) {
+    if (g.n[a] == 1) continue;
+    r = r || (g.bc[2 * a] == PPML_BC_INFLOW && o[a] - TH < 0) ||
+        (g.bc[2 * a + 1] == PPML_BC_INFLOW && o[a] + TB + TH > g.n[a]);
+  }
+  return r;
+}
+
+// The source of field f at tile-relative cell (i, j, k) whose mapped offset is off: an
+// inflow face's prescribed value where the cell lies in that face's ghost region (the later
+// axis deciding at edges and corners, as the ghost fill runs x, y, z), else the array.
+template <typename T>
+__device__ __forceinline__ const T* cell_src(const T* src, long long off, int f, const T* inflow,
+                                             const TileMaps& M, bool tin, int i, int j, int k) {
+  if (tin) {
+    int face = M.inflow[2][k + TH];
+    if (face < 0) face = M.inflow[1][j + TH];
+    if (face < 0) face = M.inflow[0][i + TH];
+    if (face >= 0) return inflow + 6 * face + f;
+  }
+  return src + off;
 }
 
 __device__ __forceinline__ long long map_off(const TileMaps& M, int i, int j, int k, int& fl) {
@@ -319,15 +356,17 @@ __device__ __forceinline__ int tbox_at(int i, int j, int k) {  // dense 18^3, co
 template <typename T>
 __device__ __forceinline__ void stage_box_maps(T* box, const T* __restrict__ src,
                                                const TileMaps& M, int tid, int flip_axis,
-                                               bool async) {
+                                               bool async, int field, const T* inflow,
+                                               bool tin) {
   int i = tid % 18, j = (tid / 18) % 18, k = tid / 324;
   for (int it = tid; it < 18 * 18 * 18; it += TN) {
     int fl;
     const long long o = map_off(M, i - 1, j - 1, k - 1, fl);
+    const T* p = tin ? cell_src(src, o, field, inflow, M, true, i - 1, j - 1, k - 1) : src + o;
     if (async) {
-      cp_async_elem(&box[it], src + o);
+      cp_async_elem(&box[it], p);
     } else {
-      const T v = src[o];
+      const T v = *p;
       box[it] = (flip_axis >= 0 && ((fl >> flip_axis) & 1)) ? -v : v;
     }
     i += 4;
@@ -552,7 +591,9 @@ __device__ __forceinline__ void line_face_velocities(const T* vb, const T* rb, i
 }
 
 // DF: the state is double-float (A.ulo / A.outlo give the low parts of rho, m, rho E).
-template <typename T, int MINB, bool DF>
+// INF: the grid has an inflow face (its ghost reads take the prescribed states; without
+// one the kernel carries none of that code).
+template <typename T, int MINB, bool DF, bool INF>
 __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LagTileSmem<T>& S = *reinterpret_cast<LagTileSmem<T>*>(smem_raw);
@@ -564,6 +605,7 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   if (!tg.valid) return;  // a padding block of a blocked order (uniform over the CTA)
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
   const bool fast_async = async_ok && tg.fast;
+  const bool tin = INF && tile_inflow(g, tg);  // some copy of this tile reads an inflow ghost
   T* const smem_t = reinterpret_cast<T*>(smem_raw);  // fld and acc are contiguous
   T* const vspace = &S.vh[0][0][0];
   // template boxes: rho, then m_a (turned into v_a in place)
@@ -601,10 +643,11 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
   static_assert(2 * 5832 <= 3 * (TB + 1) * TN, "two boxes must fit in the face-velocity space");
   if (!fast_async) {
     // boundary tiles through the maps; rho never changes sign: always asynchronous
-    stage_box_maps(rbox, A.u[0], maps, tid, -1, true);
+    stage_box_maps(rbox, A.u[0], maps, tid, -1, true, 0, A.inflow, tin);
 #pragma unroll 1
     for (int ax = 0; ax < 3; ax++)
-      if (act[ax]) stage_box_maps(vbox(ax), A.u[1 + ax], maps, tid, ax, async_ok);
+      if (act[ax])
+        stage_box_maps(vbox(ax), A.u[1 + ax], maps, tid, ax, async_ok, 1 + ax, A.inflow, tin);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -678,19 +721,37 @@ __global__ void __launch_bounds__(TN, MINB) lagrangian_tile(MarchArgs<T> A) {
       // transverse map entries) are formed once, so each copy adds one map entry.
       const long long bx = maps.off[0][a + TH], by = maps.off[1][b + TH];
       const long long base_z = bx + by;  // z line (a, b): x = a, y = b
+      if (tin) {
 #pragma unroll 4
-      for (int s = 0; s < TB; s++)
-        cp_async_elem(&S.fld[acc_at(a, b, s)], src + (base_z + maps.off[2][s + TH]));
+        for (int s = 0; s < TB; s++)
+          cp_async_elem(&S.fld[acc_at(a, b, s)],
+                        cell_src(src, base_z + maps.off[2][s + TH], f, A.inflow, maps, true, a, b, s));
+      } else {
+#pragma unroll 4
+        for (int s = 0; s < TB; s++)
+          cp_async_elem(&S.fld[acc_at(a, b, s)], src + (base_z + maps.off[2][s + TH]));
+      }
 #pragma unroll 1
       for (int ax = 0; ax < 3; ax++) {
         if (act[ax]) {
           // line (a, b) of axis ax: x line (y = a, z = b), y line (x = a, z = b), z line
           const long long base = ax == 0 ? maps.off[1][a + TH] + maps.off[2][b + TH]
                                          : (ax == 1 ? bx + maps.off[2][b + TH] : base_z);
+          if (tin) {
 #pragma unroll
-          for (int h = 0; h < HALO_POS; h++) {
-            const int p = h < 3 ? h - 3 : TB + h - 3;
-            cp_async_elem(&S.fld[halo_at(ax, h, tid)], src + (base + maps.off[ax][p + TH]));
+            for (int h = 0; h < HALO_POS; h++) {
+              const int p = h < 3 ? h - 3 : TB + h - 3;
+              int i, j, k;
+              line_cell(ax, p, a, b, i, j, k);
+              cp_async_elem(&S.fld[halo_at(ax, h, tid)],
+                            cell_src(src, base + maps.off[ax][p + TH], f, A.inflow, maps, true, i, j, k));
+            }
+          } else {
+#pragma unroll
+            for (int h = 0; h < HALO_POS; h++) {
+              const int p = h < 3 ? h - 3 : TB + h - 3;
+              cp_async_elem(&S.fld[halo_at(ax, h, tid)], src + (base + maps.off[ax][p + TH]));
+            }
           }
         }
         cp_async_commit();  // same three groups as on interior tiles
@@ -898,7 +959,7 @@ __device__ __forceinline__ int slab_at(int p, int a, int b) { return (p + TH) * 
 
 // DF: the state is double-float (A.ulo / A.outlo give the low parts of rho, m, rho E); the
 // momentum and total-energy updates are added in double-float.
-template <typename T, int MINB, bool DF>
+template <typename T, int MINB, bool DF, bool INF>
 __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EulTileSmem<T>& S = *reinterpret_cast<EulTileSmem<T>*>(smem_raw);
@@ -909,6 +970,7 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
   const TileGeom tg = tile_geom(g, tiles, A.tile_order);
   if (!tg.valid) return;  // a padding block of a blocked order (uniform over the CTA)
   const bool async_ok = !A.any_reflect;  // reflecting walls flip signs: copy through registers
+  const bool tin = INF && tile_inflow(g, tg);  // some copy of this tile reads an inflow ghost
   __shared__ TileMaps maps;
   build_maps(maps, g, tg);  // ordered by the barrier below
   double stc[4];
@@ -964,7 +1026,11 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
       int fl;
       const long long c = map_off(maps, i, j, k, fl);
       const int o = slab_at(p, s % TB, s / TB);
-      if (async_ok) {
+      if (async_ok && tin) {
+        cp_async_elem(&S.r[o], cell_src(A.u[0], c, 0, A.inflow, maps, true, i, j, k));
+        cp_async_elem(&S.m[o], cell_src(A.u[1 + ax], c, 1 + ax, A.inflow, maps, true, i, j, k));
+        cp_async_elem(&S.p[o], cell_src(A.u[5], c, 5, A.inflow, maps, true, i, j, k));
+      } else if (async_ok) {
         cp_async_elem(&S.r[o], A.u[0] + c);
         cp_async_elem(&S.m[o], A.u[1 + ax] + c);
         cp_async_elem(&S.p[o], A.u[5] + c);
@@ -982,7 +1048,8 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     int nax = -1;
     for (int q = 2; q > ax; q--)
       if (act[q]) nax = q;
-    const bool pf = async_ok && nax >= 0;
+    // (tiles that read an inflow face's ghosts stage every axis at its start instead)
+    const bool pf = async_ok && nax >= 0 && !tin;
     long long nbase = 0, nst = 0;
     if (pf) {
       int ni, nj, nk;
@@ -1121,9 +1188,9 @@ __global__ void __launch_bounds__(TN, MINB) eulerian_tile(MarchArgs<T> A) {
     T en = A.u[4][idx] - dpvs;
     T den = dpvs;  // DF: the whole FP32 decrement of rho E, added to the pair once
     if (A.phi) {
-      GridGeom gp = g;  // Phi: zero-gradient at reflecting walls, like at outflow faces
+      GridGeom gp = g;  // Phi: zero-gradient at reflecting walls and inflow faces, as at outflow
       for (int q = 0; q < 6; q++)
-        if (gp.bc[q] == 2 || gp.bc[q] == 3) gp.bc[q] = 0;
+        if (gp.bc[q] == 2 || gp.bc[q] == 3 || gp.bc[q] == PPML_BC_INFLOW) gp.bc[q] = 0;
       T m[3] = {A.out[1][idx], A.out[2][idx], A.out[3][idx]};
       const T m0[3] = {A.u[1][idx], A.u[2][idx], A.u[3][idx]};
 #pragma unroll 1

@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 PPML_OK, PPML_E_INVAL, PPML_E_CUDA, PPML_E_NONPHYSICAL, PPML_E_TIMEOUT, PPML_E_NOMEM = range(6)
 PPML_F32, PPML_F64 = 0, 1
-OUTFLOW, PERIODIC, REFLECT, HALO = 0, 1, 2, 3
+OUTFLOW, PERIODIC, REFLECT, HALO, INFLOW = 0, 1, 2, 3, 4
 HALO_PLANES = 3     # planes behind a halo face (z-slab decomposition)
 REDUCE_LEN = 10     # max|v|, max c, six sums, vacuum and non-physical counts
 FLAG_NONPHYSICAL, FLAG_DT_ZERO = 1, 2
@@ -44,7 +44,7 @@ class GridDesc(ctypes.Structure):
                 ("h", ctypes.c_double * 3), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("bc", ctypes.c_int * 6), ("dtype", ctypes.c_int),
                 ("vacuum_frac", ctypes.c_double), ("t_end", ctypes.c_double), ("flags", ctypes.c_int),
-                ("rho_ref", ctypes.c_double)]
+                ("rho_ref", ctypes.c_double), ("inflow", (ctypes.c_double * 6) * 6)]
 
 
 class State(ctypes.Structure):
@@ -149,10 +149,11 @@ def _state(fields, dtype=None, shape=None) -> State:
 
 
 class Grid:
-    """Handle over ppml_init_grid / ppml_step / ppml_cfl_dt / ppml_read_diag."""
+    """Handle over ppml_init_grid / ppml_step / ppml_cfl_dt / ppml_read_diag.
+    inflow: {face: six conserved values} for the faces whose bc is INFLOW."""
 
     def __init__(self, n, h, gamma, cfl, bc=(OUTFLOW,) * 6, dtype=PPML_F32, u0=None,
-                 vacuum_frac=1e-5, t_end=0.0, stream=None, flags=0, rho_ref=0.0):
+                 vacuum_frac=1e-5, t_end=0.0, stream=None, flags=0, rho_ref=0.0, inflow=None):
         d = GridDesc()
         d.nx, d.ny, d.nz = (int(x) for x in n)
         for a in range(3):
@@ -165,6 +166,13 @@ class Grid:
         d.t_end = float(t_end)
         d.flags = int(flags)
         d.rho_ref = float(rho_ref)
+        inflow = inflow or {}
+        for q in range(6):
+            if int(bc[q]) == INFLOW:
+                if q not in inflow:
+                    raise ValueError(f"face {q} is an inflow face without a prescribed state")
+                for f in range(6):
+                    d.inflow[q][f] = float(inflow[q][f])
         self.desc = d
         self.n = tuple(int(x) for x in n)
         self.cells = self.n[0] * self.n[1] * self.n[2]

@@ -58,6 +58,9 @@ def test_invalid_descriptors_rejected_on_host(built):
         for q, v in enumerate(kw.get("bc", (0,) * 6)):
             d.bc[q] = v
         d.dtype = kw.get("dtype", 0)
+        for q, state in kw.get("inflow", {}).items():
+            for f in range(6):
+                d.inflow[q][f] = state[f]
         h = ctypes.c_void_p()
         rc = lib.ppml_init_grid(ctypes.byref(d), None, None, ctypes.byref(h))
         return rc, lib.ppml_last_error().decode()
@@ -70,6 +73,13 @@ def test_invalid_descriptors_rejected_on_host(built):
     assert init(bc=(1, 0, 0, 0, 0, 0))[0] == ppml.PPML_E_INVAL  # unpaired periodic
     assert init(n=(8, 1, 1), bc=(0, 0, 2, 2, 0, 0))[0] == ppml.PPML_E_INVAL
     assert init(dtype=7)[0] == ppml.PPML_E_INVAL
+    assert init(bc=(5, 0, 0, 0, 0, 0))[0] == ppml.PPML_E_INVAL
+    good = {0: (1.0, 3.0, 0.0, 0.0, 7.0, 2.5)}
+    assert init(bc=(ppml.INFLOW,) + (0,) * 5, inflow={0: (0.0,) * 6})[0] == ppml.PPML_E_INVAL
+    rc, msg = init(bc=(ppml.INFLOW, 0, 2, 2, 0, 0), inflow=good)  # inflow with a wall
+    assert rc == ppml.PPML_E_INVAL and "reflecting" in msg
+    rc, msg = init(bc=(ppml.INFLOW,) + (0,) * 5, inflow=good)  # valid, but no initial state
+    assert rc == ppml.PPML_E_INVAL and "u0" in msg
     rc, msg = init()  # valid descriptor but no initial state
     assert rc == ppml.PPML_E_INVAL and "u0" in msg
     # batch validation
