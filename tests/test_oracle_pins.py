@@ -936,3 +936,34 @@ def test_inflow_face_needs_a_state():
     g = oracle.Grid((8, 1, 1), (0.125, 1.0, 1.0), 1.4, (oracle.BC_INFLOW,) + (0,) * 5)
     with pytest.raises(ValueError):
         g.desc()
+
+
+def _inflow_line(n, ax):
+    """The supersonic-inflow problem on a line along axis ax (inflow on its low face, the
+    stream's momentum in component ax)."""
+    nn = [1, 1, 1]
+    nn[ax] = n
+    shape = (nn[2], nn[1], nn[0])
+    z = np.zeros(shape)
+    u = [np.ones(shape), z, z, z, np.full(shape, 2.5), np.full(shape, 2.5)]
+    h = [1.0, 1.0, 1.0]
+    h[ax] = 1.0 / n
+    bc = [oracle.BC_OUTFLOW] * 6
+    bc[2 * ax] = oracle.BC_INFLOW
+    state = [1.0, 0.0, 0.0, 0.0, 7.0, 2.5]
+    state[1 + ax] = 3.0
+    g = oracle.Grid(tuple(nn), tuple(h), 1.4, tuple(bc), 0.4, rho_mean=1.0,
+                    inflow={2 * ax: tuple(state)})
+    out, t, steps, dg = oracle.run(g, u, 0.3)
+    return out[0].ravel(), out[1 + ax].ravel(), steps
+
+
+@pytest.mark.parametrize("ax", [1, 2])
+def test_inflow_same_along_every_axis(ax):
+    """The inflow problem along y (face 2, m_y) and z (face 4, m_z) gives the x run's
+    density and momentum profiles bit for bit, with the same steps: the face index and the
+    momentum component of an inflow state follow the axis."""
+    r0, m0, s0 = _inflow_line(200, 0)
+    r, m, s = _inflow_line(200, ax)
+    assert s == s0
+    assert np.array_equal(r, r0) and np.array_equal(m, m0)
